@@ -1,0 +1,150 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module only draws and samples input data: separable Gaussians and sine
+modes on the interior grid x_i = i/(n+1), i = 1..n, of the unit cube, returned
+as canonical (CP) tensors.  It contains none of the solver's arithmetic
+(no spectrum, no transforms, no quadrature, no truncation), so both sides can
+import it without sharing any of the method.
+
+A CP tensor is returned as ``(xi, [U_1, ..., U_d])`` with ``xi`` of shape (R,)
+and every ``U_l`` of shape (n_l, R), float64, column r of ``U_l`` being the
+mode-l vector of term r: T = sum_r xi[r] U_1[:, r] x ... x U_d[:, r].
+
+The right-hand side recipe (centres uniform in [0.3, 0.7]^d, widths uniform in
+[0.05, 0.15] or log-uniform in [lo, 0.15], amplitudes N(0, 1)) stands in for
+the paper's unstated design functions y_Omega (Section 6, Figure "Shapes of the
+right-hand side"), which are not given numerically.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 20180906
+
+
+def seed_for(config: int, problem: int = 0) -> int:
+    """Seed of problem ``problem`` of workload ``config``."""
+    return SEED_BASE + 1000 * config + problem
+
+
+def grid(n: int) -> np.ndarray:
+    """Interior nodes x_i = i h, h = 1/(n+1), i = 1..n."""
+    return np.arange(1, n + 1, dtype=np.float64) / (n + 1)
+
+
+def gaussians_cp(n: int, d: int, count: int, rng: np.random.Generator,
+                 sigma_lo: float = 0.05, sigma_hi: float = 0.15,
+                 log_sigma: bool = False):
+    """``count`` separable isotropic Gaussians a*prod_l exp(-(x_l-c_l)^2/(2 s^2))."""
+    x = grid(n)
+    centres = rng.uniform(0.3, 0.7, size=(count, d))
+    if log_sigma:
+        sig = np.exp(rng.uniform(math.log(sigma_lo), math.log(sigma_hi), size=count))
+    else:
+        sig = rng.uniform(sigma_lo, sigma_hi, size=count)
+    amp = rng.standard_normal(count)
+    U = []
+    for l in range(d):
+        U.append(np.exp(-((x[:, None] - centres[None, :, l]) ** 2) / (2.0 * sig[None, :] ** 2)))
+    return amp.astype(np.float64), U
+
+
+def sine_cp(n: int, modes) -> tuple:
+    """Rank-1 tensor prod_l sin(pi m_l x_l) sampled on the grid."""
+    x = grid(n)
+    U = [np.sin(math.pi * m * x)[:, None] for m in modes]
+    return np.ones(1), U
+
+
+def concat_cp(*cps):
+    xi = np.concatenate([c[0] for c in cps])
+    d = len(cps[0][1])
+    U = [np.concatenate([c[1][l] for c in cps], axis=1) for l in range(d)]
+    return xi, U
+
+
+@dataclass
+class Problem:
+    """One control problem (beta^2 A^-alpha + gamma A^alpha) u = b, b = beta*y_Omega."""
+    n: int
+    d: int
+    alpha: float
+    beta: float
+    gamma: float
+    y_omega: tuple = field(repr=False)   # CP (xi, [U_l])
+    eps: float = 1e-8
+    tol: float = 1e-8
+    max_rank: int = 32
+    seed: int = 0
+    label: str = ""
+
+    def rhs(self):
+        xi, U = self.y_omega
+        return self.beta * xi, U
+
+
+def config1(problem: int = 0) -> Problem:
+    """2D, n=63, alpha=0.5, beta=1, gamma=1e-2, two Gaussians; tol=eps=1e-8."""
+    s = seed_for(1, problem)
+    rng = np.random.default_rng(s)
+    y = gaussians_cp(63, 2, 2, rng)
+    return Problem(63, 2, 0.5, 1.0, 1e-2, y, eps=1e-8, tol=1e-8, max_rank=32, seed=s,
+                   label="2d_n63_a0.5_g1e-2")
+
+
+def config2(problem: int) -> Problem:
+    """3D, n=255, alpha in {0.25,0.5,0.75} x gamma in {1e-1,1e-3}; 4 Gaussians + sine."""
+    alphas = (0.25, 0.5, 0.75)
+    gammas = (1e-1, 1e-3)
+    a = alphas[problem // 2]
+    g = gammas[problem % 2]
+    s = seed_for(2, problem)
+    rng = np.random.default_rng(s)
+    y = concat_cp(gaussians_cp(255, 3, 4, rng), sine_cp(255, (1, 2, 3)))
+    return Problem(255, 3, a, 1.0, g, y, eps=1e-7, tol=1e-7, max_rank=32, seed=s,
+                   label=f"3d_n255_a{a}_g{g:g}")
+
+
+def config3(problem: int = 0) -> Problem:
+    """3D, n=1023, alpha=0.5, gamma=1e-3, 8 Gaussians."""
+    s = seed_for(3, problem)
+    rng = np.random.default_rng(s)
+    y = gaussians_cp(1023, 3, 8, rng)
+    return Problem(1023, 3, 0.5, 1.0, 1e-3, y, eps=1e-7, tol=1e-7, max_rank=48, seed=s,
+                   label="3d_n1023_a0.5_g1e-3")
+
+
+def config4(problem: int) -> Problem:
+    """One of the 512 batched 3D problems: n in {127..2047}, alpha~U[0.1,0.9],
+    gamma log-uniform in [1e-4,1], rank 1-8 Gaussians, eps=1e-6."""
+    s = seed_for(4, problem)
+    rng = np.random.default_rng(s)
+    n = int(rng.choice([127, 255, 511, 1023, 2047]))
+    a = float(rng.uniform(0.1, 0.9))
+    g = float(math.exp(rng.uniform(math.log(1e-4), 0.0)))
+    r = int(rng.integers(1, 9))
+    y = gaussians_cp(n, 3, r, rng)
+    return Problem(n, 3, a, 1.0, g, y, eps=1e-6, tol=1e-6, max_rank=32, seed=s,
+                   label=f"3d_n{n}_a{a:.3f}_g{g:.2e}")
+
+
+def config5(problem: int) -> Problem:
+    """3D, n=8191, alpha in {0.25,0.75}, gamma=1e-4, 16 Gaussians, widths
+    log-uniform in [0.01,0.15]."""
+    a = (0.25, 0.75)[problem % 2]
+    s = seed_for(5, problem)
+    rng = np.random.default_rng(s)
+    y = gaussians_cp(8191, 3, 16, rng, sigma_lo=0.01, log_sigma=True)
+    return Problem(8191, 3, a, 1.0, 1e-4, y, eps=1e-6, tol=1e-6, max_rank=64, seed=s,
+                   label=f"3d_n8191_a{a}_g1e-4")
+
+
+def random_cp(n: int, d: int, rank: int, seed: int, scale_spread: float = 0.0):
+    """Dense random CP tensor (for kernel parity tests): N(0,1) factors and weights."""
+    rng = np.random.default_rng(seed)
+    xi = rng.standard_normal(rank) * np.exp(scale_spread * rng.standard_normal(rank))
+    U = [rng.standard_normal((n, rank)) for _ in range(d)]
+    return xi, U

@@ -1,0 +1,68 @@
+"""Full-format references (paper Section 3.2, eqn:DiagFLaplace3D / 2D).
+
+solve_full:  u = (F_1 x ... x F_d) diag(1/g(rho)) (F_1 x ... x F_d) b, the exact
+             eigenbasis solve of (beta^2 A^-alpha + gamma A^alpha) u = b; d passes
+             of the 1D DST-I, a pointwise division, d passes again.
+brute_force: dense A = sum_l I x A_(l) x I (eqn_low_rank_lap), symmetric
+             eigendecomposition, A^{+-alpha} by the spectral definition
+             (eqn:frac_Oper), dense solve.  Independent of the DST; n <= 16.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .spectrum import dst1, eigenvalues, laplacian_1d
+from .quadrature import g_control, rho_full
+
+
+def dst_all(Y: np.ndarray) -> np.ndarray:
+    for ax in range(Y.ndim):
+        Y = dst1(Y, axis=ax)
+    return Y
+
+
+def apply_g_full(Y: np.ndarray, gfun) -> np.ndarray:
+    """F g(Lambda) F y for a full tensor y (eqn:DiagFLaplace3D)."""
+    lams = [eigenvalues(m) for m in Y.shape]
+    return dst_all(dst_all(Y) * gfun(rho_full(lams)))
+
+
+def solve_full(b: np.ndarray, alpha, beta, gamma_) -> np.ndarray:
+    """Exact solution u* of (beta^2 A^-alpha + gamma A^alpha) u = b."""
+    return apply_g_full(b, lambda r: 1.0 / g_control(r, alpha, beta, gamma_))
+
+
+def apply_full(x: np.ndarray, alpha, beta, gamma_) -> np.ndarray:
+    """(beta^2 A^-alpha + gamma A^alpha) x in full format."""
+    return apply_g_full(x, lambda r: g_control(r, alpha, beta, gamma_))
+
+
+def dense_laplacian(ns) -> np.ndarray:
+    """A = sum_l I x ... x A_(l) x ... x I with axis 0 = mode 1 fastest-varying
+    last in numpy C order (A acts on x.reshape(-1) of an array of shape ns)."""
+    d = len(ns)
+    N = int(np.prod(ns))
+    A = np.zeros((N, N))
+    for l in range(d):
+        mats = [np.eye(m) for m in ns]
+        mats[l] = laplacian_1d(ns[l])
+        K = mats[0]
+        for M in mats[1:]:
+            K = np.kron(K, M)
+        A += K
+    return A
+
+
+def brute_force_solve(b: np.ndarray, alpha, beta, gamma_) -> np.ndarray:
+    """Dense eigendecomposition solve (eqn:frac_Oper), no DST involved."""
+    A = dense_laplacian(b.shape)
+    w, V = np.linalg.eigh(A)
+    Mop = V @ np.diag(beta**2 * w ** (-alpha) + gamma_ * w**alpha) @ V.T
+    return np.linalg.solve(Mop, b.reshape(-1)).reshape(b.shape)
+
+
+def brute_force_power(ns, s) -> np.ndarray:
+    """Dense A^s by the spectral definition (eqn:frac_Oper)."""
+    A = dense_laplacian(ns)
+    w, V = np.linalg.eigh(A)
+    return V @ np.diag(w**s) @ V.T

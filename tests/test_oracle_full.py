@@ -1,0 +1,64 @@
+"""Pins of the oracle's full-format solve (Section 3.2, eqn:DiagFLaplace3D) against brute
+force by dense eigendecomposition (spectral definition of A^alpha, Section 2) and against
+manufactured sine-mode solutions."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import full
+
+
+@pytest.mark.parametrize("ns", [(5, 7), (4, 3, 5), (8, 8)])
+@pytest.mark.parametrize("alpha,beta,gamma_", [(0.5, 1.0, 1e-2), (0.25, 2.0, 1e-1), (1.0, 1.0, 1e-3)])
+def test_full_solve_matches_brute_force(ns, alpha, beta, gamma_):
+    rng = np.random.default_rng(sum(ns))
+    b = rng.standard_normal(ns)
+    u = full.solve_full(b, alpha, beta, gamma_)
+    ub = full.brute_force_solve(b, alpha, beta, gamma_)
+    assert np.linalg.norm(u - ub) <= 1e-12 * np.linalg.norm(ub)
+
+
+def test_dense_laplacian_is_kronecker_sum_of_5_point_stencil():
+    """A acts as the 5-point stencil / h^2 on the interior grid (Section 3.2)."""
+    n = 6
+    h = 1.0 / (n + 1)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((n, n))
+    A = full.dense_laplacian([n, n])
+    y = (A @ x.reshape(-1)).reshape(n, n)
+    xp = np.pad(x, 1)
+    st = (4 * xp[1:-1, 1:-1] - xp[:-2, 1:-1] - xp[2:, 1:-1] - xp[1:-1, :-2] - xp[1:-1, 2:]) / h**2
+    assert np.allclose(y, st, rtol=0, atol=1e-9 * np.abs(st).max())
+
+
+@pytest.mark.parametrize("modes", [(1, 2, 3), (5, 1, 7), (2, 2)])
+def test_manufactured_sine_mode(modes):
+    """A sampled product of sines is an eigenvector of A with eigenvalue sum_l lambda_{m_l}."""
+    n = 31
+    d = len(modes)
+    x = np.arange(1, n + 1) / (n + 1)
+    b = np.ones([n] * d)
+    for l, m in enumerate(modes):
+        shape = [1] * d
+        shape[l] = n
+        b = b * np.sin(math.pi * m * x).reshape(shape)
+    A = None  # eigenvalue from the stencil, not from the closed form
+    v = np.sin(math.pi * np.arange(1, n + 1)[:, None] * x[None, :])
+    rho = 0.0
+    for m in modes:
+        vm = np.sin(math.pi * m * x)
+        lap = (2 * vm - np.concatenate([[0], vm[:-1]]) - np.concatenate([vm[1:], [0]])) * (n + 1) ** 2
+        rho += lap[0] / vm[0]
+    alpha, beta, gamma_ = 0.5, 1.5, 1e-2
+    g = beta**2 * rho ** (-alpha) + gamma_ * rho**alpha
+    u = full.solve_full(b, alpha, beta, gamma_)
+    assert np.linalg.norm(u - b / g) <= 1e-12 * np.linalg.norm(b / g)
+    del A, v
+
+
+def test_apply_then_solve_is_identity():
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal((9, 10, 11))
+    u = full.solve_full(b, 0.3, 1.0, 1e-2)
+    assert np.linalg.norm(full.apply_full(u, 0.3, 1.0, 1e-2) - b) <= 1e-12 * np.linalg.norm(b)
