@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Throughput of the low-rank (CP) PCG control solve on one GB300, in 3D control solves/s.
+
+Workload (one step): the six 3D problems d=3, n=255 (16.6M grid points each),
+alpha in {0.25, 0.5, 0.75} x gamma in {1e-1, 1e-3}, beta = 1, right-hand side y_Omega =
+4 seeded separable Gaussians + sin(pi x) sin(2 pi y) sin(3 pi z) (CP rank 5), truncation
+eps = PCG tol = 1e-7, CP rank cap 32.  Each problem's operator set-up (symbol and
+preconditioner CP factors, workspace) is done once before timing, as a library user
+would for repeated solves with one operator; the timed step is the full Algorithm 1
+(PCG with RHOSVD truncation) for all six right-hand sides.
+
+`value`  : device-resident solves/s (CUDA events on the launching stream, L2 flushed
+           between steps with a 512 MiB write, outside the events).
+`e2e`    : the same through the public API with host buffers: every step copies the
+           right-hand sides from pinned host memory and reads the solutions back.
+Accuracy : after timing, every solution is compared with the library's full-format
+           FP64 eigenbasis solve (16.6M points), and the largest relative L2 error is
+           reported; a run whose error exceeds 1e-6 exits non-zero.
+`--impl reference` times the CPU FP64 oracle on the same workload (one problem per
+step, cycling) on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D control solves/s at rel-err<=1e-6 (plain FP64, CP-PCG)"
+UNIT = "solves/s"
+WORKLOAD = "3d_n255_6problems_alpha{0.25,0.5,0.75}_gamma{1e-1,1e-3}_rank5rhs_eps1e-7"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--problems", type=int, default=6)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def problems(count):
+    import fc_inputs as fi
+    return [fi.config2(p % 6) for p in range(count)]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_solve(prob):
+    """One CP-PCG solve by the CPU FP64 oracle (symbols built as part of the solve)."""
+    from oracle import pcg, quadrature as q
+    fs = q.control_symbol(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, 1e-10)
+    ps = q.precond_symbol(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, 24)
+    return pcg.pcg(fs, ps, prob.rhs(), prob.eps, prob.tol, prob.max_rank)
+
+
+def cpu_baseline(probs, budget_s=25.0):
+    """Oracle solves/s on a bounded sample (problems in order until ~budget_s)."""
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(probs):
+        cpu_oracle_solve(probs[done])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of the {len(probs)} n=255 3D problems, CP-PCG (numpy/scipy FP64, "
+                      f"BLAS threads <= {cores}), symbol set-up included, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    probs = problems(6)
+    for i in range(args.warmup):
+        cpu_oracle_solve(probs[i % 6])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        cpu_oracle_solve(probs[i % 6])
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one oracle solve (problems cycled)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} single-problem oracle solves"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_1809_01971_gb300 as fc
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    probs = problems(args.problems)
+    # independent problems: each rank solves the full six-problem set (weak scaling)
+    hs, Bs, Us = [], [], []
+    for p in probs:
+        h = fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank)
+        hs.append(h)
+        Bs.append(fc.CP.from_factors(*p.rhs(), device=dev))
+        Us.append(fc.CP(p.d, p.n, p.max_rank, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        infos = []
+        for p, h, B, U in zip(probs, hs, Bs, Us):
+            infos.append(fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=stream))
+        return infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    launches0 = fc.fc_launch_count()
+    iters = []
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append([i.iters for i in infos])
+    barrier()
+    launches = fc.fc_launch_count() - launches0
+    clocks = sampler.stop()
+    t_total = sum(times) / 1e3
+    if world > 1:
+        t = torch.tensor([t_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    solves = len(probs) * args.steps * world
+    value = solves / t_total
+
+    # end to end through the public API with host buffers
+    host_in = []
+    for p in probs:
+        xi, U = p.rhs()
+        host_in.append((torch.tensor(xi).pin_memory(),
+                        torch.tensor(np.stack([u.T for u in U])).pin_memory()))
+    host_out = [(torch.empty(p.max_rank, dtype=torch.float64).pin_memory(),
+                 torch.empty(p.d, p.max_rank, p.n, dtype=torch.float64).pin_memory()) for p in probs]
+    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_in)
+    d2h = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_out)
+
+    def e2e_step():
+        for (xi_h, U_h), (xo, Uo), p, h, B, U in zip(host_in, host_out, probs, hs, Bs, Us):
+            R = xi_h.numel()
+            B.xi[:R].copy_(xi_h, non_blocking=True)
+            B.U[:, :R, :p.n].copy_(U_h, non_blocking=True)
+            B.rank = R
+            fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=stream)
+            xo.copy_(U.xi[:p.max_rank], non_blocking=True)
+            Uo.copy_(U.U[:, :p.max_rank, :p.n], non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
+    e2e_times = []
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    barrier()
+    e2e_t = sum(e2e_times) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_t], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = solves / e2e_t
+
+    # accuracy against the library's full-format FP64 eigenbasis solve
+    max_err = 0.0
+    nn = probs[0].n ** 3
+    full_b = torch.empty(nn, dtype=torch.float64, device=dev)
+    full_u = torch.empty_like(full_b)
+    tmp = torch.empty_like(full_b)
+    for p, h, B, U in zip(probs, hs, Bs, Us):
+        fb = fc.fc_to_full(h, B, out=full_b)
+        fc.fc_full_solve(h, full_b, full_u, tmp)
+        ucp = fc.fc_to_full(h, U, out=tmp)
+        err = float(torch.linalg.norm(ucp.reshape(-1) - full_u) / torch.linalg.norm(full_u))
+        max_err = max(max_err, err)
+        del fb
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "problems_per_step": len(probs),
+                           "l2": "flushed between steps (512 MiB write, untimed)",
+                           "setup": "per operator, before timing",
+                           "pcg_iters": iters[-1]},
+                "max_rel_err_vs_full": max_err,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches),
+                "clocks": clocks,
+                "roofline": None,
+                "cpu_baseline": None}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(probs)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0 if max_err <= 1e-6 else 3
+
+
+if __name__ == "__main__":
+    sys.exit(main())

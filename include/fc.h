@@ -1,0 +1,176 @@
+/*
+ * fc.h — C ABI of libfc, a GB300 (sm_103a) library for the low-rank PCG solve of the
+ * fractional optimal-control equation
+ *
+ *        (beta^2 A^-alpha + gamma A^alpha) u = b,      b = beta * y_Omega,
+ *
+ * of Heidel, Khoromskaia, Khoromskij and Schulz, "Tensor product method for fast solution
+ * of optimal control problems with fractional multidimensional Laplacian in constraints"
+ * (arXiv:1809.01971).  Multiplying eqn:forControl (Section 3.1) by beta gives this form.
+ *
+ * A is the finite-difference Dirichlet Laplacian on the n^d interior grid of (0,1)^d,
+ * h = 1/(n+1) (Section 3.2): A = sum_l I x .. x A_(l) x .. x I, A_(l) = h^-2 tridiag(-1,2,-1),
+ * A_(l) = F Lambda F with F the orthonormal DST-I, F[j,k] = sqrt(2/(n+1)) sin(pi j k/(n+1)),
+ * lambda_k = (4/h^2) sin^2(pi k/(2(n+1))) (eqn:eig_lap).
+ *
+ * Conventions for every entry point
+ *  - All pointers named dev_* or held in fc_cp are DEVICE pointers; *_host are host pointers.
+ *    The caller owns every buffer it passes (including the workspace).  The handle owns only
+ *    its setup tables, which fc_setup allocates with cudaMalloc and fc_destroy frees.
+ *  - A CP (canonical) tensor (eqn:CP_form, Section 5) is
+ *        T = sum_{r<rank} xi[r] U_1[:,r] (x) ... (x) U_d[:,r],
+ *    with xi (length >= cap) and factor matrices U_l (column-major, leading dimension ld >= n,
+ *    at least cap columns) in FP64 device memory.  Columns need not be normalised on input.
+ *  - Outputs whose cap is too small get FC_ERANK and y->rank set to the rank needed.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *    enqueued on it; entry points that return a value to the host (fc_inner, fc_truncate's
+ *    rank, fc_solve) synchronise that stream before returning.  Outputs are undefined on error.
+ *  - Return value: FC_OK (0) or a negative FC_E* code; fc_strerror() names it.  No C++
+ *    exception crosses the ABI, no kernel traps; CUDA errors are mapped to FC_ECUDA.
+ */
+#ifndef FC_H
+#define FC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FC_OK = 0,
+    FC_EINVAL = -1,       /* bad argument (d, n, alpha, beta, gamma, eps, null pointer)   */
+    FC_ERANK = -2,        /* output capacity too small / rank cap overflow                */
+    FC_ENOCONV = -3,      /* PCG reached k_max before the tolerance                       */
+    FC_EBREAKDOWN = -4,   /* <P,S> <= 0: truncation destroyed positive definiteness       */
+    FC_ENAN = -5,         /* non-finite scalar in the recurrences                          */
+    FC_ECUDA = -6,        /* CUDA runtime error (message via fc_last_cuda_error)           */
+    FC_EWORKSPACE = -7,   /* no workspace bound, or bound workspace too small              */
+    FC_ESETUP = -8        /* quadrature / preconditioner construction failed               */
+};
+
+typedef struct fc_ctx* fc_handle;
+
+/* CP tensor descriptor (eqn:CP_form).  d in {2,3}; all modes have the same size n. */
+typedef struct fc_cp {
+    int d;
+    int n;
+    int rank;      /* number of terms (input: used; output: written)            */
+    int cap;       /* allocated number of columns / weights                      */
+    int ld;        /* leading dimension of every U[l], ld >= n                   */
+    double* xi;    /* device, cap weights                                        */
+    double* U[3];  /* device, U[l] is ld x cap column-major; U[2] unused if d==2 */
+} fc_cp;
+
+/* Setup options; pass NULL for defaults (values in brackets). */
+typedef struct fc_setup_opts {
+    double delta_sym;   /* target relative accuracy of the operator symbol [1e-10]          */
+    int precond_rank;   /* rank R_P of the exponential-sum preconditioner fit [24]           */
+    int max_rank;       /* largest CP rank of any iterate after truncation [32]              */
+    int max_tucker;     /* largest Tucker rank per mode inside the truncation [48]           */
+    int max_input_rank; /* largest rank of a right-hand side / fc_apply input [max_rank]     */
+} fc_setup_opts;
+
+typedef struct fc_setup_info {
+    int n, d;
+    int rank_symbol;    /* R_A = R_minus + d * R_plus (eqn:Func_of_rho, Lemma 4.1)           */
+    int rank_minus;     /* nodes of the exponential sum for rho^-alpha                        */
+    int rank_plus;      /* nodes of the exponential sum for rho^(alpha-1)                     */
+    int rank_precond;   /* R_P                                                                */
+    double rho_min, rho_max;
+    double sym_err;     /* max relative error of the symbol on a geometric rho grid          */
+    double pc_err;      /* max |p(rho) g(rho) - 1| of the preconditioner on that grid        */
+    size_t workspace_bytes;
+} fc_setup_info;
+
+typedef struct fc_solve_opts {
+    double tol;         /* stop when ||R||/||B|| <= tol (recursive residual) [1e-8]          */
+    double eps;         /* truncation accuracy; <= 0 means the eps given to fc_setup         */
+    int kmax;           /* iteration limit [100]                                              */
+    int max_rank;       /* CP rank cap of the iterates; <= 0 means the fc_setup value         */
+} fc_solve_opts;
+
+typedef struct fc_solve_info {
+    int status;         /* FC_OK, FC_ENOCONV, FC_EBREAKDOWN, FC_ENAN                          */
+    int iters;
+    double relres;      /* last recursive ||R^(k+1)|| / ||B||                                 */
+    int rank_x;         /* CP rank of the returned solution                                   */
+    int max_rank_seen;  /* largest CP rank of any truncated iterate                           */
+    int trunc_calls;
+    double history[128];/* relres per iteration (first min(iters,128))                       */
+} fc_solve_info;
+
+/* Build the spectrum (eqn:eig_lap), the CP symbol of beta^2 rho^-alpha + gamma rho^alpha by
+ * sinc quadrature of the Laplace transform (Section 4.2, eqn:Sinc_quadr_trunc, eqn:Func_of_rho;
+ * the positive power through Lemma 4.1), and the exponential-sum preconditioner of 1/g.
+ * Requires 0 < alpha <= 1, beta > 0, gamma > 0, d in {2,3}, 1 <= n <= 4095, eps > 0.
+ * Allocates the handle's device tables (cudaMalloc on the current device). */
+int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
+             const fc_setup_opts* opts, fc_handle* out);
+
+/* Sizes and accuracy figures of a handle. */
+int fc_get_info(fc_handle h, fc_setup_info* info);
+
+/* Bytes of device scratch that fc_apply/fc_precond/fc_truncate/fc_inner/fc_solve need. */
+int fc_workspace_size(fc_handle h, size_t* bytes);
+
+/* Bind caller-owned device scratch (>= fc_workspace_size bytes, 256-byte aligned). The
+ * handle keeps the pointer; calls on one handle must not overlap in time. */
+int fc_set_workspace(fc_handle h, void* dev_ptr, size_t bytes);
+
+/* Copy the operator symbol (which=0), or the preconditioner symbol (which=1), as a CP tensor
+ * in the eigen-index domain: diag(g(Lambda)) ~ sum_k xi_k E_1[:,k] x .. x E_d[:,k] with
+ * E_l[i,k] a function of lambda_i (eqn:Func_of_rho).  out->cap must be >= the symbol rank. */
+int fc_get_symbol(fc_handle h, int which, fc_cp* out, void* stream);
+
+/* y = (beta^2 A^-alpha + gamma A^alpha) x in CP form, untruncated: rank R_A * x->rank,
+ * term (k, j) at column k * x->rank + j (eqn:Lap2DtimesX / eqn:Lap3DtimesX, Section 3.2):
+ * y = sum_{k,j} xi_k eta_j (x)_l F (e_lk . F x_lj).  The DST runs as a sine-matrix product. */
+int fc_apply(fc_handle h, const fc_cp* x, fc_cp* y, void* stream);
+
+/* y = P(A) x with the rank-R_P preconditioner symbol (Section 3.3, precond of Algorithm 1);
+ * rank R_P * x->rank, same layout as fc_apply. */
+int fc_precond(fc_handle h, const fc_cp* x, fc_cp* y, void* stream);
+
+/* y = trunc(x, eps) (Section 5: RHOSVD canonical -> Tucker -> canonical; d=2 the reduced
+ * SVD).  Per mode the leading left singular subspace of the weighted side matrix
+ * U_l diag(|xi|) is kept up to eps ||xi||_2 / sqrt(2d) in Frobenius norm (at most max_tucker
+ * columns), the Tucker core is formed, and its canonical terms (d=3: mode-3 rotation then
+ * slice SVDs) are dropped smallest first while their norm stays <= eps ||core|| / sqrt(2),
+ * keeping at most max_rank.  normalize != 0 first rescales every column to unit norm.
+ * Result columns are unit vectors, weights positive and descending.  Synchronises. */
+int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int normalize,
+                fc_cp* y, void* stream);
+
+/* *out_host = <x, y> = sum_{k,j} xi_k eta_j prod_l <x_lk, y_lj> (inner products of
+ * Algorithm 1).  Synchronises. */
+int fc_inner(fc_handle h, const fc_cp* x, const fc_cp* y, double* out_host, void* stream);
+
+/* Algorithm 1 (low-rank PCG, Section 3.3) with X^(0) = 0 for (beta^2 A^-alpha + gamma A^alpha)
+ * u = rhs; every update is truncated with fc_truncate's rule.  u->cap >= max_rank.
+ * Returns FC_OK or the failure status (also in info->status). */
+int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* opts,
+             fc_solve_info* info, void* stream);
+
+/* Expand a CP tensor to the full n^d array, column-major (i_1 fastest). */
+int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream);
+
+/* Full-format eigenbasis solve u = (F x..x F) diag(1/g(rho)) (F x..x F) rhs with the exact
+ * symbol g(rho) = beta^2 rho^-alpha + gamma rho^alpha (eqn:DiagFLaplace3D, Section 3.2);
+ * rhs and u are n^d column-major device arrays (may alias). Needs n^d doubles of workspace
+ * beyond fc_workspace_size: pass it as dev_tmp. */
+int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev_tmp,
+                  void* stream);
+
+void fc_destroy(fc_handle h);
+const char* fc_strerror(int code);
+const char* fc_last_cuda_error(void);
+
+/* Number of CUDA kernels libfc has launched in this process so far (all handles, all
+ * devices); a host-side counter for instrumentation, no synchronisation. */
+unsigned long long fc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FC_H */

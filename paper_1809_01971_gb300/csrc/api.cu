@@ -1,0 +1,779 @@
+// libfc C ABI: handle, setup, workspace, and the host orchestration of the low-rank PCG
+// (Algorithm 1 of Section 3.3) over the device kernels.  Every arithmetic step of the
+// path runs in device kernels; the host only sequences launches, reads back ranks and
+// the FP64 PCG scalars.
+#include "../../include/fc.h"
+#include "fc_common.cuh"
+#include "fc_kernels.h"
+#include "setup_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace fc;
+
+#include <atomic>
+
+namespace fc {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace fc
+
+namespace {
+
+thread_local std::string g_cuda_msg;
+
+int cuda_fail(cudaError_t e) {
+    g_cuda_msg = cudaGetErrorString(e);
+    return FC_ECUDA;
+}
+#define CK(x)                                        \
+    do {                                             \
+        cudaError_t _e = (x);                        \
+        if (_e != cudaSuccess) return cuda_fail(_e); \
+    } while (0)
+#define CKL()                                                 \
+    do {                                                      \
+        cudaError_t _e = cudaGetLastError();                  \
+        if (_e != cudaSuccess) return cuda_fail(_e);          \
+    } while (0)
+
+// Internal CP tensor: factor matrices of one tensor are contiguous, mode stride = ld * cap.
+struct CP {
+    int rank = 0, cap = 0, ld = 0;
+    double* xi = nullptr;
+    double* U[3] = {nullptr, nullptr, nullptr};
+    long long bs() const { return (long long)ld * cap; }
+};
+
+// Linear bump allocator over the caller's workspace (256-byte aligned slices).
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0, cap = 0;
+    bool count_only = true;
+    void* take(size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        void* p = count_only ? nullptr : base + off;
+        off += bytes;
+        return p;
+    }
+    double* d(size_t count) { return (double*)take(count * sizeof(double)); }
+    int* i(size_t count) { return (int*)take(count * sizeof(int)); }
+};
+
+}  // namespace
+
+struct fc_ctx {
+    int n = 0, d = 0;
+    double alpha = 0, beta = 0, gamma = 0, eps = 0;
+    fc_setup_opts opts{};
+    fc_setup_info info{};
+    int RA = 0, RP = 0;   // symbol / preconditioner ranks
+    int CAP = 0;          // CP rank cap of the iterates
+    int KIN = 0;          // largest input rank of apply/precond/truncate
+    int RM = 0;           // max Tucker rank
+    int CM = kMaxC;       // sketch width
+    int QMAX = 0;         // largest output rank of a truncation
+    long long KMAX = 0;   // largest number of terms entering a truncation
+    // device tables (owned)
+    double* tables = nullptr;
+    double *lam = nullptr, *sintab = nullptr;
+    double *xiA = nullptr, *EA = nullptr, *GEA = nullptr;   // symbol CP and mode Grams
+    double *xiP = nullptr, *EP = nullptr, *GEP = nullptr;   // preconditioner CP and Grams
+    // workspace (caller-owned)
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    // workspace slices
+    struct {
+        double *Y, *Y2, *Q, *tmp, *M, *Tm, *GY, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *wK;
+        double *corep, *core, *G3, *ev3, *W3, *Srot, *SG, *mus, *Vs, *sigma, *X, *Yh;
+        double *scal, *Mi;
+        int *dims, *tslice, *tidx;
+        CP cat, Xs, Rs, Ps, Zs, Ss;
+        double* pinned_dummy;
+    } w{};
+    int splits = 1;
+    unsigned long long seed = 0x1809019710ull;
+    // host pinned scalars for readback
+    double* hbuf = nullptr;
+    int* hint = nullptr;
+};
+
+namespace {
+
+size_t layout(fc_ctx* h, Arena& a) {
+    const int n = h->n, d = h->d, CM = h->CM, RM = h->RM;
+    const long long K = h->KMAX;
+    auto& w = h->w;
+    const size_t nC = (size_t)n * CM;
+    w.Y = a.d(3 * nC);
+    w.Y2 = a.d(3 * nC);
+    w.Q = a.d(3 * nC);
+    w.tmp = a.d(3 * nC);
+    w.M = a.d(3 * (size_t)CM * CM);
+    w.Tm = a.d(3 * (size_t)CM * CM);
+    w.GY = a.d(3 * (size_t)n * n);
+    w.GQ = a.d(3 * nC);
+    w.Tr = a.d(3 * (size_t)CM * CM);
+    w.theta = a.d(3 * (size_t)CM);
+    w.Vr = a.d(3 * (size_t)CM * CM);
+    w.Z = a.d(3 * (size_t)n * RM);
+    w.Zr = a.d(3 * (size_t)n * RM);
+    w.C = a.d(3 * (size_t)std::max(RM, CM) * K);
+    w.wK = a.d((size_t)K);
+    w.corep = a.d((size_t)h->splits * RM * RM * RM);
+    w.core = a.d((size_t)RM * RM * RM);
+    w.G3 = a.d((size_t)RM * RM);
+    w.ev3 = a.d((size_t)RM);
+    w.W3 = a.d((size_t)RM * RM);
+    w.Srot = a.d((size_t)RM * RM * RM);
+    w.SG = a.d((size_t)RM * RM * RM);
+    w.mus = a.d((size_t)RM * RM);
+    w.Vs = a.d((size_t)RM * RM * RM);
+    w.sigma = a.d((size_t)RM * RM);
+    w.X = a.d(3 * (size_t)RM * h->QMAX);
+    w.Yh = a.d(3 * (size_t)n * h->KIN);
+    w.scal = a.d(64);
+    w.Mi = a.d(3 * (size_t)h->KIN * h->KIN);
+    w.dims = a.i(D_SIZE);
+    w.tslice = a.i((size_t)RM * RM);
+    w.tidx = a.i((size_t)RM * RM);
+    auto mkcp = [&](CP& c, int cap) {
+        c.cap = cap; c.ld = n; c.rank = 0;
+        c.xi = a.d(cap);
+        double* U = a.d((size_t)3 * n * cap);
+        for (int l = 0; l < 3; ++l) c.U[l] = U ? U + (size_t)l * n * cap : nullptr;
+    };
+    mkcp(w.cat, std::max(2 * h->CAP, h->KIN));
+    mkcp(w.Xs, h->CAP);
+    mkcp(w.Rs, std::max(h->CAP, h->KIN));
+    mkcp(w.Ps, h->CAP);
+    mkcp(w.Zs, h->CAP);
+    mkcp(w.Ss, h->CAP);
+    (void)d;
+    return a.off + 256;
+}
+
+CP from_user(const fc_cp* x) {
+    CP c;
+    c.rank = x->rank; c.cap = x->cap; c.ld = x->ld; c.xi = x->xi;
+    for (int l = 0; l < 3; ++l) c.U[l] = x->U[l];
+    return c;
+}
+
+bool check_cp(const fc_ctx* h, const fc_cp* x, bool output) {
+    if (!x) return false;
+    if (x->d != h->d || x->n != h->n || x->ld < h->n || x->cap < 0) return false;
+    if (!output && (x->rank < 0 || x->rank > x->cap)) return false;
+    if (x->cap > 0 && (!x->xi || !x->U[0] || !x->U[1] || (h->d == 3 && !x->U[2]))) return false;
+    return true;
+}
+
+// DST-I of `cols` columns of every mode: out_l = F in_l (Section 3.2, F = F^T = F^{-1})
+void dst_cols(fc_ctx* h, cudaStream_t st, int cols, const double* const in[3], int ldi,
+              double* const out[3], int ldo) {
+    if (cols <= 0) return;
+    LdSine F{h->sintab, 2 * (h->n + 1)};
+    for (int l = 0; l < h->d; ++l)
+        gemm(st, h->n, cols, h->n, F, LdN{in[l], ldi, 0}, 1.0, 0.0, out[l], ldo);
+}
+
+struct KRIn {           // implicit Khatri-Rao tensor sum_{k,j} xa_k xb_j (x)_l E_l[:,k].Yh_l[:,j]
+    const double* xa; const double* E; int Ra; long long bsE; const double* GE;
+    const double* xb; const double* Yh; int S;
+};
+struct DenseIn { const double* w; const double* U; int ld; long long bs; int K; };
+
+// ---------------------------------------------------------------------------------------
+// Truncation (Section 5, RHOSVD canonical -> Tucker -> canonical).  Input either an
+// implicit Khatri-Rao tensor in the eigen-index domain (mat-vec outputs; the Tucker bases
+// are transformed back with one DST of their r_l columns) or explicit factors.  Output
+// written to `out` (rank set after a stream synchronisation).
+// ---------------------------------------------------------------------------------------
+int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn, double eps,
+                  int maxq, CP& out) {
+    auto& w = h->w;
+    const int n = h->n, d = h->d, CM = h->CM, RM = h->RM;
+    const long long nC = (long long)n * CM;
+    const long long K = kr ? (long long)kr->Ra * kr->S : dn->K;
+    if (K <= 0) { out.rank = 0; return FC_OK; }
+    if (K > h->KMAX) return FC_ERANK;
+    maxq = std::min(maxq, std::min(out.cap, h->QMAX));
+    const int c = (int)std::min<long long>(K, CM);
+    const unsigned long long seed = (h->seed += 0x9E3779B97F4A7C15ull);
+    int* dims = w.dims;
+    CK(cudaMemsetAsync(dims, 0, sizeof(int) * D_SIZE, st));
+
+    // ---- stage 1: range of the weighted side matrices W_l --------------------------------
+    if (kr) {
+        if (K <= CM)
+            launch_kr_cols(st, d, n, kr->Ra, kr->S, kr->E, n, kr->bsE, kr->xa,
+                           kr->Yh, n, (long long)n * h->KIN, kr->xb, 1, w.Y, n, nC);
+        else
+            launch_sketch_kr(st, d, n, kr->Ra, kr->S, c, kr->E, n, kr->bsE, kr->xa,
+                             kr->Yh, n, (long long)n * h->KIN, kr->xb, seed, w.Y, n, nC, w.tmp);
+    } else {
+        if (K <= CM)
+            launch_scale_cols_abs(st, d, n, (int)K, dn->U, dn->ld, dn->bs, dn->w, w.Y, n, nC);
+        else
+            launch_sketch_dense(st, d, n, (int)K, c, dn->U, dn->ld, dn->bs, dn->w, seed, w.Y, n, nC);
+    }
+    CKL();
+    // three Cholesky-QR passes with diagonal pivoting: Q = orth(Y) (span preserved)
+    double* src = w.Y;
+    double* dst = w.Q;
+    const long long CC = (long long)CM * CM;
+    for (int pass = 0; pass < 3; ++pass) {
+        gemm(st, c, c, n, LdT{src, n, nC}, LdN{src, n, nC}, 1.0, 0.0, w.M, CM, CC, d);
+        launch_pchol(st, d, w.M, CM, CC, nullptr, 0, c, 1e-15, w.Tm, CM, CC, dims + D_C1, 1);
+        gemm(st, n, c, c, LdN{src, n, nC}, LdN{w.Tm, CM, CC}, 1.0, 0.0, dst, n, nC, d);
+        std::swap(src, dst);
+        if (pass == 0) dst = w.Y2;
+    }
+    double* Qb = src;   // orthonormal basis, live columns dims[D_C1 + l]
+    CKL();
+    // Rayleigh-Ritz matrix T = Q^T W W^T Q and energy tr = ||W||_F^2
+    if (kr) {
+        // GY = Yh diag(xb^2) Yh^T ;  T = Q^T (GE . GY) Q
+        const long long nn = (long long)n * n;
+        gemm(st, n, n, kr->S, LdSq{kr->Yh, n, (long long)n * h->KIN, kr->xb},
+             LdT{kr->Yh, n, (long long)n * h->KIN}, 1.0, 0.0, w.GY, n, nn, d);
+        gemm(st, n, c, n, LdHad{kr->GE, w.GY, n, nn, nn}, LdN{Qb, n, nC}, 1.0, 0.0, w.GQ, n, nC, d);
+        gemm(st, c, c, n, LdT{Qb, n, nC}, LdN{w.GQ, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+        launch_trace_kr(st, d, n, kr->GE, n, nn, w.GY, n, nn, w.scal + 0);
+        launch_kr_wnorm(st, kr->Ra, kr->xa, kr->S, kr->xb, w.scal + 4);
+    } else {
+        // Bq = Q^T W (c x K) in w.C (ld CM ... reuse C region), T = Bq Bq^T
+        double* Bq = w.C;
+        gemm(st, c, (int)K, n, LdT{Qb, n, nC}, LdAbsN{dn->U, dn->ld, dn->bs, dn->w}, 1.0, 0.0, Bq,
+             CM, (long long)CM * K, d);
+        gemm(st, c, c, (int)K, LdN{Bq, CM, (long long)CM * K}, LdT{Bq, CM, (long long)CM * K}, 1.0,
+             0.0, w.Tr, CM, CC, d);
+        launch_weighted_energy(st, d, n, (int)K, dn->U, dn->ld, dn->bs, dn->w, w.scal + 0);
+        launch_sumsq(st, (int)K, dn->w, w.scal + 4, 1);
+    }
+    CKL();
+    launch_jacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, c, w.theta, CM, w.Vr, CM, CC);
+    // Tucker ranks: tail <= eps ||w||_2 / sqrt(2d)
+    launch_select_tucker(st, d, w.theta, CM, w.scal + 0, w.scal + 4, eps * eps / (2.0 * d),
+                         std::min(RM, c), dims + D_R, w.scal + 8, dims + D_C1);
+    launch_stage2_dims(st, d, dims);
+    // Z_l = Q_l Vr_l[:, :RM]
+    const int rz = std::min(RM, c);
+    const long long nR = (long long)n * RM;
+    gemm(st, n, rz, c, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nR, d);
+    CKL();
+    // C_l = Z_l^T U_l  (r_l x K), unweighted factors
+    const long long RK = (long long)RM * K;
+    for (int l = 0; l < d; ++l) {
+        if (kr)
+            gemm(st, RM, (int)K, n, LdT{w.Z + l * nR, n, 0},
+                 LdKR{kr->E + l * kr->bsE, n, 0, kr->Yh + (long long)l * n * h->KIN, n, 0, kr->S},
+                 1.0, 0.0, w.C + l * RK, RM, 0, 1, dims + D_R + l);
+        else
+            gemm(st, RM, (int)K, n, LdT{w.Z + l * nR, n, 0}, LdN{dn->U + l * dn->bs, dn->ld, 0}, 1.0,
+                 0.0, w.C + l * RK, RM, 0, 1, dims + D_R + l);
+    }
+    // signed term weights
+    const double* wK = dn ? dn->w : w.wK;
+    if (kr) launch_outer_weights(st, kr->Ra, kr->xa, kr->S, kr->xb, w.wK);
+    CKL();
+    // ---- core: B3[(a + r0 b), c] = sum_K w_K C0[a,K] C1[b,K] C2[c,K] ----------------------
+    const int RR = RM * RM;
+    int splits = (int)std::min<long long>(h->splits, std::max<long long>(1, K / 128));
+    double* coreOut = (splits > 1) ? w.corep : w.core;
+    LdCore A{w.C, w.C + RK, wK, RM, dims + D_R};
+    if (d == 3)
+        gemm(st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, RM, 0}, 1.0, 0.0, coreOut, RR, 0, 1,
+             dims + D_R12, dims + D_R3, nullptr, splits, (long long)RR * RM);
+    else
+        gemm(st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, coreOut, RR, 0, 1, dims + D_R12, nullptr,
+             nullptr, splits, (long long)RR * RM);
+    if (splits > 1) {
+        // reduce partials: core = sum_s corep[s]
+        // (use a GEMM with K = 1 and B = ones to sum; rows = RR*RM flattened)
+        gemm(st, RR * RM, 1, 1, LdPart{w.corep, splits, (long long)RR * RM}, LdOnes{}, 1.0, 0.0,
+             w.core, RR * RM);
+    }
+    CKL();
+    launch_core_energy(st, d, w.core, RR, dims, w.scal + 12);
+    // mode-3 rotation: G3 = B3^T B3, W3 = eigvecs, Srot = B3 W3
+    gemm(st, RM, RM, RR, LdT{w.core, RR, 0}, LdN{w.core, RR, 0}, 1.0, 0.0, w.G3, RM, 0, 1,
+         dims + D_R3, dims + D_R3, dims + D_R12);
+    launch_jacobi(st, 1, w.G3, RM, 0, dims + D_R3, 0, RM, w.ev3, 0, w.W3, RM, 0);
+    gemm(st, RR, RM, RM, LdN{w.core, RR, 0}, LdN{w.W3, RM, 0}, 1.0, 0.0, w.Srot, RR, 0, 1,
+         dims + D_R12, dims + D_R3, dims + D_R3);
+    // slice Grams SG[s] = S_s^T S_s  (S_s = r0 x r1, compact column s of Srot)
+    gemm(st, RM, RM, RM, LdSlT{w.Srot, RR, dims + D_R}, LdSl{w.Srot, RR, dims + D_R}, 1.0, 0.0,
+         w.SG, RM, RR, (d == 3) ? RM : 1, dims + D_R + 1, dims + D_R + 1, dims + D_R);
+    launch_jacobi(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR);
+    CKL();
+    launch_select_terms(st, w.mus, RM, dims + D_R3, dims + D_NPER, RM, RM, w.scal + 12,
+                        eps * eps / 2.0, maxq, dims + D_Q, w.sigma, w.tslice, w.tidx, w.scal + 16);
+    const long long RQ = (long long)RM * h->QMAX;
+    launch_gather_terms(st, d, RM, dims, dims + D_Q, maxq, w.sigma, w.tslice, w.tidx, w.Srot, RR,
+                        w.W3, RM, w.Vs, RM, RR, w.X, RM, RQ);
+    CKL();
+    // ---- output factors U'_l = Z_l X_l (eigen-index domain: F (Z_l X_l)) ------------------
+    const double* Zuse = w.Z;
+    if (kr) {
+        const double* in[3] = {w.Z, w.Z + nR, w.Z + 2 * nR};
+        double* o[3] = {w.Zr, w.Zr + nR, w.Zr + 2 * nR};
+        dst_cols(h, st, rz, in, n, o, n);
+        Zuse = w.Zr;
+    }
+    for (int l = 0; l < d; ++l)
+        gemm(st, n, maxq, RM, LdN{Zuse + l * nR, n, 0}, LdN{w.X + l * RQ, RM, 0}, 1.0, 0.0,
+             out.U[l], out.ld, 0, 1, nullptr, dims + D_Q, dims + D_R + l);
+    CK(cudaMemcpyAsync(out.xi, w.sigma, sizeof(double) * maxq, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->hint, dims, sizeof(int) * D_SIZE, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out.rank = h->hint[D_Q];
+    return FC_OK;
+}
+
+// Khatri-Rao input from a CP tensor x and a symbol: Yh = F x (DST of the x factors)
+int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, bool precond, KRIn& kr) {
+    if (x.rank > h->KIN) return FC_ERANK;
+    const long long nK = (long long)h->n * h->KIN;
+    const double* in[3] = {x.U[0], x.U[1], x.U[2]};
+    double* o[3] = {h->w.Yh, h->w.Yh + nK, h->w.Yh + 2 * nK};
+    dst_cols(h, st, x.rank, in, x.ld, o, h->n);
+    kr.xa = precond ? h->xiP : h->xiA;
+    kr.E = precond ? h->EP : h->EA;
+    kr.Ra = precond ? h->RP : h->RA;
+    kr.bsE = (long long)h->n * kr.Ra;
+    kr.GE = precond ? h->GEP : h->GEA;
+    kr.xb = x.xi;
+    kr.Yh = h->w.Yh;
+    kr.S = x.rank;
+    // the E arrays use batch stride n * RA for both symbols (see fc_setup)
+    return FC_OK;
+}
+
+int inner_impl(fc_ctx* h, cudaStream_t st, const CP& x, const CP& y, double* out) {
+    if (x.rank == 0 || y.rank == 0) { *out = 0.0; return FC_OK; }
+    if (x.rank > h->KIN || y.rank > h->KIN) return FC_ERANK;
+    const long long kk = (long long)h->KIN * h->KIN;
+    for (int l = 0; l < h->d; ++l)
+        gemm(st, x.rank, y.rank, h->n, LdT{x.U[l], x.ld, 0}, LdN{y.U[l], y.ld, 0}, 1.0, 0.0,
+             h->w.Mi + l * kk, x.rank);
+    launch_inner_reduce(st, h->d, x.rank, y.rank, x.xi, y.xi, h->w.Mi, x.rank, kk, h->w.scal + 20);
+    CKL();
+    CK(cudaMemcpyAsync(h->hbuf, h->w.scal + 20, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *out = h->hbuf[0];
+    return FC_OK;
+}
+
+// out = trunc(a*x + b*y) with column normalisation (CP linear combination of Algorithm 1)
+int combo_trunc(fc_ctx* h, cudaStream_t st, const CP& x, double a, const CP* y, double b,
+                double eps, int maxq, CP& out) {
+    Piece p0{x.xi, {x.U[0], x.U[1], x.U[2]}, x.ld, x.rank, a};
+    Piece p1{nullptr, {nullptr, nullptr, nullptr}, 0, 0, 0.0};
+    if (y) p1 = Piece{y->xi, {y->U[0], y->U[1], y->U[2]}, y->ld, y->rank, b};
+    const int K = p0.K + p1.K;
+    if (K > h->w.cat.cap) return FC_ERANK;
+    CP& cat = h->w.cat;
+    launch_concat_normalize(st, h->d, h->n, p0, p1, cat.U[0], cat.ld, cat.bs(), cat.xi);
+    CKL();
+    cat.rank = K;
+    DenseIn dn{cat.xi, cat.U[0], cat.ld, cat.bs(), K};
+    return truncate_impl(h, st, nullptr, &dn, eps, maxq, out);
+}
+
+int kr_trunc(fc_ctx* h, cudaStream_t st, const CP& x, bool precond, double eps, int maxq, CP& out) {
+    KRIn kr;
+    int rc = kr_from(h, st, x, precond, kr);
+    if (rc) return rc;
+    return truncate_impl(h, st, &kr, nullptr, eps, maxq, out);
+}
+
+}  // namespace
+
+// =========================================================================================
+extern "C" {
+
+const char* fc_strerror(int code) {
+    switch (code) {
+        case FC_OK: return "ok";
+        case FC_EINVAL: return "invalid argument";
+        case FC_ERANK: return "rank capacity exceeded";
+        case FC_ENOCONV: return "PCG did not converge within kmax iterations";
+        case FC_EBREAKDOWN: return "PCG breakdown: <P, S> <= 0 after truncation";
+        case FC_ENAN: return "non-finite PCG scalar";
+        case FC_ECUDA: return "CUDA error";
+        case FC_EWORKSPACE: return "workspace missing or too small";
+        case FC_ESETUP: return "quadrature or preconditioner construction failed";
+        default: return "unknown error";
+    }
+}
+
+const char* fc_last_cuda_error(void) { return g_cuda_msg.c_str(); }
+
+unsigned long long fc_launch_count(void) { return fc::g_launches.load(std::memory_order_relaxed); }
+
+int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
+             const fc_setup_opts* o, fc_handle* out) {
+    if (!out) return FC_EINVAL;
+    *out = nullptr;
+    if (!(d == 2 || d == 3) || n < 1 || n > 4095 || !(alpha > 0.0 && alpha <= 1.0) ||
+        !(beta > 0.0) || !(gamma > 0.0) || !(eps > 0.0) || !std::isfinite(beta) ||
+        !std::isfinite(gamma))
+        return FC_EINVAL;
+    fc_setup_opts opts{1e-10, 24, 32, 48, 0};
+    if (o) {
+        if (o->delta_sym > 0) opts.delta_sym = o->delta_sym;
+        if (o->precond_rank > 0) opts.precond_rank = o->precond_rank;
+        if (o->max_rank > 0) opts.max_rank = o->max_rank;
+        if (o->max_tucker > 0) opts.max_tucker = o->max_tucker;
+        if (o->max_input_rank > 0) opts.max_input_rank = o->max_input_rank;
+    }
+    opts.max_tucker = std::min(opts.max_tucker, kMaxC - 8);
+    opts.max_rank = std::min(opts.max_rank, opts.max_tucker * opts.max_tucker);
+    if (opts.max_input_rank <= 0) opts.max_input_rank = opts.max_rank;
+    SymbolNodes sym, pc;
+    if (!build_control_nodes(n, d, alpha, beta, gamma, opts.delta_sym, sym)) return FC_ESETUP;
+    if (!build_precond_nodes(n, d, alpha, beta, gamma, opts.precond_rank, pc)) return FC_ESETUP;
+    fc_ctx* h = new (std::nothrow) fc_ctx();
+    if (!h) return FC_EINVAL;
+    h->n = n; h->d = d; h->alpha = alpha; h->beta = beta; h->gamma = gamma; h->eps = eps;
+    h->opts = opts;
+    h->RA = (int)sym.tau.size();
+    h->RP = (int)pc.tau.size();
+    h->CAP = opts.max_rank;
+    h->KIN = std::max(opts.max_input_rank, opts.max_rank);
+    h->RM = opts.max_tucker;
+    h->QMAX = std::max(h->CAP, h->KIN);
+    h->KMAX = std::max<long long>({(long long)h->RA * h->KIN, (long long)h->RP * h->KIN,
+                                   2LL * h->CAP, (long long)h->KIN});
+    h->splits = 32;
+    // device tables
+    const int N = n + 1;
+    const int RAm = std::max(h->RA, h->RP);
+    size_t tcount = (size_t)n + 2 * N + h->RA + h->RP + 2 * 3 * (size_t)n * RAm + 2 * 3 * (size_t)n * n;
+    if (cudaMalloc(&h->tables, tcount * sizeof(double)) != cudaSuccess) {
+        delete h;
+        return FC_ECUDA;
+    }
+    double* p = h->tables;
+    h->lam = p; p += n;
+    h->sintab = p; p += 2 * N;
+    h->xiA = p; p += h->RA;
+    h->xiP = p; p += h->RP;
+    h->EA = p; p += 3 * (size_t)n * RAm;
+    h->EP = p; p += 3 * (size_t)n * RAm;
+    h->GEA = p; p += 3 * (size_t)n * n;
+    h->GEP = p; p += 3 * (size_t)n * n;
+    // the symbols use a common mode stride n * RA (EA) so KRIn can address both identically
+    std::vector<double> lam = spectrum(n);
+    std::vector<double> tab(2 * N);
+    const double sc = std::sqrt(2.0 / N);
+    for (int m = 0; m < 2 * N; ++m) {
+        // sin(pi m / N) with the argument reduced into [0, pi/2] for accuracy
+        int mm = m % (2 * N);
+        double sgn = 1.0;
+        if (mm >= N) { mm -= N; sgn = -1.0; }
+        if (2 * mm > N) mm = N - mm;
+        tab[m] = sc * sgn * std::sin(M_PI * mm / N);
+    }
+    cudaStream_t st = 0;
+    int rc = FC_OK;
+    int *dmode = nullptr;
+    double *dtau = nullptr, *dw = nullptr;
+    const int RT = h->RA + h->RP;
+    std::vector<double> tau(RT), wv(RT);
+    std::vector<int> mode(RT);
+    for (int k = 0; k < h->RA; ++k) { tau[k] = sym.tau[k]; wv[k] = sym.w[k]; mode[k] = sym.mode[k]; }
+    for (int k = 0; k < h->RP; ++k) { tau[h->RA + k] = pc.tau[k]; wv[h->RA + k] = pc.w[k]; mode[h->RA + k] = -1; }
+    do {
+        if (cudaMemcpy(h->lam, lam.data(), sizeof(double) * n, cudaMemcpyHostToDevice) ||
+            cudaMemcpy(h->sintab, tab.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice)) { rc = FC_ECUDA; break; }
+        if (cudaMalloc(&dtau, sizeof(double) * RT) || cudaMalloc(&dw, sizeof(double) * RT) ||
+            cudaMalloc(&dmode, sizeof(int) * RT)) { rc = FC_ECUDA; break; }
+        cudaMemcpy(dtau, tau.data(), sizeof(double) * RT, cudaMemcpyHostToDevice);
+        cudaMemcpy(dw, wv.data(), sizeof(double) * RT, cudaMemcpyHostToDevice);
+        cudaMemcpy(dmode, mode.data(), sizeof(int) * RT, cudaMemcpyHostToDevice);
+        const long long bsE = (long long)n * h->RA;
+        const long long bsP = (long long)n * h->RP;
+        launch_build_symbol(st, n, d, h->lam, dtau, dw, dmode, h->RA, h->EA, n, bsE, h->xiA);
+        launch_build_symbol(st, n, d, h->lam, dtau + h->RA, dw + h->RA, dmode + h->RA, h->RP, h->EP,
+                            n, bsP, h->xiP);
+        // mode Grams GE_l = E_l diag(xi^2) E_l^T  (weighted side-matrix Grams of the symbols)
+        const long long nn = (long long)n * n;
+        gemm(st, n, n, h->RA, LdSq{h->EA, n, bsE, h->xiA}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GEA, n, nn, d);
+        gemm(st, n, n, h->RP, LdSq{h->EP, n, bsP, h->xiP}, LdT{h->EP, n, bsP}, 1.0, 0.0, h->GEP, n, nn, d);
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { rc = FC_ECUDA; break; }
+    } while (0);
+    cudaFree(dtau); cudaFree(dw); cudaFree(dmode);
+    if (rc == FC_OK && (cudaMallocHost(&h->hbuf, 64 * sizeof(double)) != cudaSuccess ||
+                        cudaMallocHost(&h->hint, 64 * sizeof(int)) != cudaSuccess))
+        rc = FC_ECUDA;
+    if (rc != FC_OK) {
+        fc_destroy(h);
+        return rc;
+    }
+    // precond symbol's E uses mode stride n*RP; KRIn uses n*RA for E: store a view note
+    fc_setup_info& I = h->info;
+    I.n = n; I.d = d;
+    I.rank_symbol = h->RA; I.rank_minus = sym.r_minus; I.rank_plus = sym.r_plus;
+    I.rank_precond = h->RP;
+    I.rho_min = sym.rho_min; I.rho_max = sym.rho_max;
+    I.sym_err = sym.err; I.pc_err = pc.err;
+    Arena a;
+    I.workspace_bytes = layout(h, a);
+    *out = h;
+    return FC_OK;
+}
+
+int fc_get_info(fc_handle h, fc_setup_info* info) {
+    if (!h || !info) return FC_EINVAL;
+    *info = h->info;
+    return FC_OK;
+}
+
+int fc_workspace_size(fc_handle h, size_t* bytes) {
+    if (!h || !bytes) return FC_EINVAL;
+    *bytes = h->info.workspace_bytes;
+    return FC_OK;
+}
+
+int fc_set_workspace(fc_handle h, void* dev_ptr, size_t bytes) {
+    if (!h || !dev_ptr || bytes < h->info.workspace_bytes) return FC_EWORKSPACE;
+    if (((uintptr_t)dev_ptr & 255) != 0) return FC_EINVAL;
+    Arena a;
+    a.base = (char*)dev_ptr;
+    a.cap = bytes;
+    a.count_only = false;
+    layout(h, a);
+    h->ws = (char*)dev_ptr;
+    h->ws_bytes = bytes;
+    return FC_OK;
+}
+
+int fc_get_symbol(fc_handle h, int which, fc_cp* out, void* stream) {
+    if (!h || !out || !(which == 0 || which == 1) || !check_cp(h, out, true)) return FC_EINVAL;
+    const int R = which ? h->RP : h->RA;
+    if (out->cap < R) { out->rank = R; return FC_ERANK; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* xi = which ? h->xiP : h->xiA;
+    const double* E = which ? h->EP : h->EA;
+    const long long bs = (long long)h->n * R;
+    CK(cudaMemcpyAsync(out->xi, xi, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
+    for (int l = 0; l < h->d; ++l)
+        CK(cudaMemcpy2DAsync(out->U[l], sizeof(double) * out->ld, E + l * bs, sizeof(double) * h->n,
+                             sizeof(double) * h->n, R, cudaMemcpyDeviceToDevice, st));
+    out->rank = R;
+    CK(cudaStreamSynchronize(st));
+    return FC_OK;
+}
+
+static int apply_common(fc_handle h, const fc_cp* x, fc_cp* y, void* stream, bool precond) {
+    if (!h || !check_cp(h, x, false) || !check_cp(h, y, true)) return FC_EINVAL;
+    if (!h->ws) return FC_EWORKSPACE;
+    const int R = precond ? h->RP : h->RA;
+    const long long K = (long long)R * x->rank;
+    if (K > y->cap) { y->rank = (int)std::min<long long>(K, 0x7fffffff); return FC_ERANK; }
+    cudaStream_t st = (cudaStream_t)stream;
+    CP xc = from_user(x);
+    KRIn kr;
+    int rc = kr_from(h, st, xc, precond, kr);
+    if (rc) return rc;
+    // y_l = F (E_l[:,k] . Yh_l[:,j]) for all (k, j), weights xa_k xb_j
+    LdSine F{h->sintab, 2 * (h->n + 1)};
+    const long long bsE = (long long)h->n * R;
+    for (int l = 0; l < h->d; ++l)
+        gemm(st, h->n, (int)K, h->n, F,
+             LdKR{kr.E + l * bsE, h->n, 0, kr.Yh + (long long)l * h->n * h->KIN, h->n, 0, kr.S}, 1.0,
+             0.0, y->U[l], y->ld);
+    launch_outer_weights(st, R, kr.xa, kr.S, kr.xb, y->xi);
+    CKL();
+    y->rank = (int)K;
+    CK(cudaStreamSynchronize(st));
+    return FC_OK;
+}
+
+int fc_apply(fc_handle h, const fc_cp* x, fc_cp* y, void* stream) {
+    return apply_common(h, x, y, stream, false);
+}
+int fc_precond(fc_handle h, const fc_cp* x, fc_cp* y, void* stream) {
+    return apply_common(h, x, y, stream, true);
+}
+
+int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int normalize, fc_cp* y,
+                void* stream) {
+    if (!h || !check_cp(h, x, false) || !check_cp(h, y, true) || !(eps >= 0.0) || max_rank < 1)
+        return FC_EINVAL;
+    if (!h->ws) return FC_EWORKSPACE;
+    if (x->rank > h->w.cat.cap || x->rank > h->KMAX) { y->rank = x->rank; return FC_ERANK; }
+    cudaStream_t st = (cudaStream_t)stream;
+    CP xc = from_user(x), yc = from_user(y);
+    int rc;
+    if (normalize) {
+        rc = combo_trunc(h, st, xc, 1.0, nullptr, 0.0, eps, max_rank, yc);
+    } else {
+        // copy into the contiguous concat buffer as given (no normalisation)
+        CP& cat = h->w.cat;
+        for (int l = 0; l < h->d; ++l)
+            CK(cudaMemcpy2DAsync(cat.U[l], sizeof(double) * cat.ld, x->U[l], sizeof(double) * x->ld,
+                                 sizeof(double) * h->n, x->rank, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(cat.xi, x->xi, sizeof(double) * x->rank, cudaMemcpyDeviceToDevice, st));
+        DenseIn dn{cat.xi, cat.U[0], cat.ld, cat.bs(), x->rank};
+        rc = truncate_impl(h, st, nullptr, &dn, eps, max_rank, yc);
+    }
+    y->rank = yc.rank;
+    return rc;
+}
+
+int fc_inner(fc_handle h, const fc_cp* x, const fc_cp* y, double* out_host, void* stream) {
+    if (!h || !out_host || !check_cp(h, x, false) || !check_cp(h, y, false)) return FC_EINVAL;
+    if (!h->ws) return FC_EWORKSPACE;
+    return inner_impl(h, (cudaStream_t)stream, from_user(x), from_user(y), out_host);
+}
+
+int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
+             fc_solve_info* info, void* stream) {
+    if (!h || !check_cp(h, rhs, false) || !check_cp(h, u, true)) return FC_EINVAL;
+    if (!h->ws) return FC_EWORKSPACE;
+    fc_solve_opts opts{1e-8, 0.0, 100, 0};
+    if (o) opts = *o;
+    if (!(opts.tol > 0.0)) opts.tol = 1e-8;
+    if (opts.kmax <= 0) opts.kmax = 100;
+    const double eps = (opts.eps > 0.0) ? opts.eps : h->eps;
+    const int cap = std::min(h->CAP, (opts.max_rank > 0) ? opts.max_rank : h->CAP);
+    if (u->cap < cap) { u->rank = cap; return FC_ERANK; }
+    if (rhs->rank > h->KIN) return FC_ERANK;
+    fc_solve_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    cudaStream_t st = (cudaStream_t)stream;
+    auto& w = h->w;
+    CP B = from_user(rhs);
+    CP &X = w.Xs, &R = w.Rs, &P = w.Ps, &Z = w.Zs, &S = w.Ss;
+    int rc;
+    double bn2;
+    if ((rc = inner_impl(h, st, B, B, &bn2))) return rc;
+    X.rank = 0;
+    auto finish = [&](int status) -> int {
+        inf.status = status;
+        inf.rank_x = X.rank;
+        // copy X to the caller's u
+        for (int l = 0; l < h->d; ++l)
+            if (X.rank > 0)
+                CK(cudaMemcpy2DAsync(u->U[l], sizeof(double) * u->ld, X.U[l], sizeof(double) * X.ld,
+                                     sizeof(double) * h->n, X.rank, cudaMemcpyDeviceToDevice, st));
+        if (X.rank > 0)
+            CK(cudaMemcpyAsync(u->xi, X.xi, sizeof(double) * X.rank, cudaMemcpyDeviceToDevice, st));
+        u->rank = X.rank;
+        CK(cudaStreamSynchronize(st));
+        if (info) *info = inf;
+        return status;
+    };
+    if (!(bn2 > 0.0)) return finish(std::isfinite(bn2) ? FC_OK : FC_ENAN);
+    const double bn = std::sqrt(bn2);
+    // R0 = B (normalised columns, same tensor), X0 = 0
+    {
+        Piece p0{B.xi, {B.U[0], B.U[1], B.U[2]}, B.ld, B.rank, 1.0};
+        Piece p1{nullptr, {nullptr, nullptr, nullptr}, 0, 0, 0.0};
+        launch_concat_normalize(st, h->d, h->n, p0, p1, R.U[0], R.ld, R.bs(), R.xi);
+        CKL();
+        R.rank = B.rank;
+    }
+    auto track = [&](const CP& c) { inf.max_rank_seen = std::max(inf.max_rank_seen, c.rank); ++inf.trunc_calls; };
+    if ((rc = kr_trunc(h, st, R, true, eps, cap, Z))) return rc;           // Z0 = trunc(precond(R0))
+    track(Z);
+    // P0 = Z0
+    for (int l = 0; l < h->d; ++l)
+        CK(cudaMemcpyAsync(P.U[l], Z.U[l], sizeof(double) * h->n * Z.rank, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(P.xi, Z.xi, sizeof(double) * Z.rank, cudaMemcpyDeviceToDevice, st));
+    P.rank = Z.rank;
+    double rz;
+    if ((rc = inner_impl(h, st, R, Z, &rz))) return rc;
+    for (int k = 0; k < opts.kmax; ++k) {
+        if ((rc = kr_trunc(h, st, P, false, eps, cap, S))) return rc;        // S = trunc(fun(P))
+        track(S);
+        double ps;
+        if ((rc = inner_impl(h, st, P, S, &ps))) return rc;
+        if (!std::isfinite(ps) || !std::isfinite(rz)) { inf.iters = k; return finish(FC_ENAN); }
+        if (!(ps > 0.0)) { inf.iters = k; return finish(FC_EBREAKDOWN); }
+        const double a = rz / ps;                                             // alpha_k
+        if (X.rank == 0) {
+            if ((rc = combo_trunc(h, st, P, a, nullptr, 0.0, eps, cap, X))) return rc;
+        } else {
+            if ((rc = combo_trunc(h, st, X, 1.0, &P, a, eps, cap, X))) return rc;  // X + alpha P
+        }
+        track(X);
+        if ((rc = combo_trunc(h, st, R, 1.0, &S, -a, eps, cap, R))) return rc;     // R - alpha S
+        track(R);
+        double rr;
+        if ((rc = inner_impl(h, st, R, R, &rr))) return rc;
+        const double rel = std::sqrt(std::max(rr, 0.0)) / bn;
+        if (k < 128) inf.history[k] = rel;
+        inf.iters = k + 1;
+        inf.relres = rel;
+        if (!std::isfinite(rel)) return finish(FC_ENAN);
+        if (rel <= opts.tol) return finish(FC_OK);
+        if ((rc = kr_trunc(h, st, R, true, eps, cap, Z))) return rc;          // Z = trunc(precond(R))
+        track(Z);
+        double rzn;
+        if ((rc = inner_impl(h, st, R, Z, &rzn))) return rc;
+        const double b = rzn / rz;                                            // beta_k
+        if ((rc = combo_trunc(h, st, Z, 1.0, &P, b, eps, cap, P))) return rc;  // P = Z + beta P
+        track(P);
+        rz = rzn;
+    }
+    return finish(FC_ENOCONV);
+}
+
+int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream) {
+    if (!h || !dev_dense || !check_cp(h, x, false)) return FC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_to_full(st, h->d, h->n, x->rank, x->xi, x->U[0], x->U[1], h->d == 3 ? x->U[2] : x->U[1],
+                   x->ld, dev_dense);
+    CKL();
+    CK(cudaStreamSynchronize(st));
+    return FC_OK;
+}
+
+int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev_tmp, void* stream) {
+    if (!h || !dev_rhs || !dev_u || !dev_tmp) return FC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = h->n;
+    LdSine F{h->sintab, 2 * (n + 1)};
+    const long long nn = (long long)n * n;
+    // y = (F x .. x F) x  by d axis passes of a sine-matrix product
+    auto dst_all = [&](const double* in, double* out) -> int {
+        if (h->d == 2) {
+            gemm(st, n, n, n, F, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);            // axis 0
+            gemm(st, n, n, n, LdN{dev_tmp, n, 0}, F, 1.0, 0.0, out, n);           // axis 1
+        } else {
+            gemm(st, n, (int)nn, n, F, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);      // axis 0
+            gemm(st, n, n, n, LdN{dev_tmp, n, nn}, F, 1.0, 0.0, out, n, nn, n);   // axis 1 per i3
+            gemm(st, (int)nn, n, n, LdN{out, (int)nn, 0}, F, 1.0, 0.0, dev_tmp, (int)nn);  // axis 2
+            CK(cudaMemcpyAsync(out, dev_tmp, sizeof(double) * nn * n, cudaMemcpyDeviceToDevice, st));
+        }
+        return FC_OK;
+    };
+    int rc = dst_all(dev_rhs, dev_u);
+    if (rc) return rc;
+    launch_full_scale(st, h->d, n, h->lam, h->alpha, h->beta, h->gamma, dev_u);
+    rc = dst_all(dev_u, dev_u);
+    if (rc) return rc;
+    CKL();
+    CK(cudaStreamSynchronize(st));
+    return FC_OK;
+}
+
+void fc_destroy(fc_handle h) {
+    if (!h) return;
+    if (h->tables) cudaFree(h->tables);
+    if (h->hbuf) cudaFreeHost(h->hbuf);
+    if (h->hint) cudaFreeHost(h->hint);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,228 @@
+// Shared device helpers of libfc: the FP64 tiled GEMM with operand loaders, reductions,
+// and launch-wrapper declarations.  All matrices are column-major.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FC_DEV __device__ __forceinline__
+
+namespace fc {
+
+// Count of kernels launched by this library in this process (fc_launch_count).
+void note_launch();
+
+constexpr int kMaxC = 64;       // largest dense eigen / Cholesky problem handled by one CTA
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------------------
+// Operand loaders.  op(A) is M x K, op(B) is K x N; a loader returns element (i, k) of the
+// operand for batch item b.  Plain matrices are column-major with leading dimension ld and
+// batch stride bs (elements).
+// ---------------------------------------------------------------------------------------
+struct LdN {  // op(X) = X
+    const double* p; int ld; long long bs;
+    FC_DEV double operator()(int i, int k, int b) const { return p[b * bs + i + (long long)k * ld]; }
+};
+struct LdT {  // op(X) = X^T
+    const double* p; int ld; long long bs;
+    FC_DEV double operator()(int i, int k, int b) const { return p[b * bs + k + (long long)i * ld]; }
+};
+// Orthonormal DST-I matrix F[i,k] = sqrt(2/N) sin(pi (i+1)(k+1)/N) from a table
+// tab[m] = sqrt(2/N) sin(pi m / N), m = 0..2N-1 (Section 3.2).
+struct LdSine {
+    const double* tab; int N2;
+    FC_DEV double operator()(int i, int k, int) const {
+        long long m = (long long)(i + 1) * (k + 1);
+        return tab[m % N2];
+    }
+};
+// Khatri-Rao column (k,j) -> e_k . y_j, column index kj = k*S + j, row i (Section 3.2,
+// the mode factors of eqn:Lap3DtimesX in the eigenbasis).  Batch b selects the mode.
+struct LdKR {
+    const double* E; int lde; long long bsE;
+    const double* Y; int ldy; long long bsY;
+    int S;
+    FC_DEV double operator()(int i, int kj, int b) const {
+        int k = kj / S, j = kj - k * S;
+        return E[b * bsE + i + (long long)k * lde] * Y[b * bsY + i + (long long)j * ldy];
+    }
+};
+// Rows (a,b) of the mode-(1,2) unfolding of a CP tensor's projected factors:
+// A[(a + r1*b), K] = w_K C1[a,K] C2[b,K]  (core assembly, eqn:coret with a CP input).
+struct LdCore12 {
+    const double* C1; const double* C2; const double* w; int ldc; int r1;
+    FC_DEV double operator()(int ab, int K, int) const {
+        int b = ab / r1, a = ab - b * r1;
+        return w[K] * C1[a + (long long)K * ldc] * C2[b + (long long)K * ldc];
+    }
+};
+// A[a, K] = w_K C1[a, K]  (2D core: (C1 diag(w)) C2^T)
+struct LdScaledN {
+    const double* p; int ld; const double* w;
+    FC_DEV double operator()(int i, int k, int) const { return w[k] * p[i + (long long)k * ld]; }
+};
+
+
+// ---- further operand loaders used by the truncation --------------------------------------
+struct LdSq {     // w_k^2 * X[i, k]
+    const double* p; int ld; long long bs; const double* w;
+    FC_DEV double operator()(int i, int k, int b) const { return w[k] * w[k] * p[b * bs + i + (long long)k * ld]; }
+};
+struct LdAbsN {   // |w_k| * X[i, k]
+    const double* p; int ld; long long bs; const double* w;
+    FC_DEV double operator()(int i, int k, int b) const { return fabs(w[k]) * p[b * bs + i + (long long)k * ld]; }
+};
+struct LdHad {    // A[i, k] * B[i, k]  (n x n Hadamard product of two Grams)
+    const double* A; const double* B; int n; long long bsA, bsB;
+    FC_DEV double operator()(int i, int k, int b) const {
+        return A[b * bsA + i + (long long)k * n] * B[b * bsB + i + (long long)k * n];
+    }
+};
+// A[(a + r0 b), k] = w_k C0[a, k] C1[b, k], r0 read from device memory
+struct LdCore {
+    const double* C0; const double* C1; const double* w; int ldc; const int* r0p;
+    FC_DEV double operator()(int ab, int k, int) const {
+        int r0 = *r0p; int b = ab / r0, a = ab - b * r0;
+        return w[k] * C0[a + (long long)k * ldc] * C1[b + (long long)k * ldc];
+    }
+};
+struct LdOnes { FC_DEV double operator()(int, int, int) const { return 1.0; } };
+struct LdPart {   // sum of S partial results (split-K reduction), element i
+    const double* p; int S; long long stride;
+    FC_DEV double operator()(int i, int, int) const {
+        double s = 0; for (int t = 0; t < S; ++t) s += p[t * stride + i]; return s;
+    }
+};
+// slice s of a compact (r0 x r1) column: element (a, b) = S[s*ld + a + r0*b]
+struct LdSlT {    // op = slice^T : (b, a)
+    const double* S; long long ld; const int* r0p;
+    FC_DEV double operator()(int b, int a, int s) const { return S[s * ld + a + (long long)(*r0p) * b]; }
+};
+struct LdSl {     // op = slice : (a, b)
+    const double* S; long long ld; const int* r0p;
+    FC_DEV double operator()(int a, int b, int s) const { return S[s * ld + a + (long long)(*r0p) * b]; }
+};
+
+// ---------------------------------------------------------------------------------------
+// C[b] = alpha * op(A)[b] * op(B)[b] + beta * C[b]   (M x N, inner K), FP64.
+// Sizes can come from device memory (dM/dN/dK non-null) so that one launch covers the
+// largest case and blocks outside the live size return.  Split-K: gridDim.z = batch*splits,
+// split s handles K range [s*kchunk, (s+1)*kchunk) and writes C + s*splitStride (the caller
+// reduces the partials).  Register tile 4x4 per thread, 64x64 block tile, BK = 16.
+// ---------------------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <class LA, class LB>
+__global__ void __launch_bounds__(256)
+gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
+            LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
+            int batch, int splits, int kchunk, long long splitStride)
+{
+    __shared__ double As[GBK][GBM + 1];
+    __shared__ double Bs[GBK][GBN + 1];
+    if (dM) M = min(M, *dM);
+    if (dN) N = min(N, *dN);
+    if (dK) K = min(K, *dK);
+    const int zb = blockIdx.z / splits, zs = blockIdx.z - zb * splits;
+    const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+    if (m0 >= M || n0 >= N || zb >= batch) return;
+    int kbeg = zs * kchunk, kend = min(K, kbeg + kchunk);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+        // 64 x 16 tile of op(A): 1024 elements, 4 per thread
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int e = threadIdx.x + t * 256;
+            int ii = e & 63, kk = e >> 6;
+            int gi = m0 + ii, gk = k0 + kk;
+            As[kk][ii] = (gi < M && gk < kend) ? A(gi, gk, zb) : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int e = threadIdx.x + t * 256;
+            int kk = e & 15, jj = e >> 4;
+            int gj = n0 + jj, gk = k0 + kk;
+            Bs[kk][jj] = (gj < N && gk < kend) ? B(gk, gj, zb) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double* Cb = C + zb * bsC + zs * splitStride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gi = m0 + ty + 16 * i;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gj = n0 + tx + 16 * j;
+            if (gj >= N) continue;
+            double* c = Cb + gi + (long long)gj * ldc;
+            *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+        }
+    }
+}
+
+template <class LA, class LB>
+inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha, double beta,
+                 double* C, int ldc, long long bsC = 0, int batch = 1,
+                 const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr,
+                 int splits = 1, long long splitStride = 0)
+{
+    if (M <= 0 || N <= 0 || batch <= 0) return;
+    int kchunk = K;
+    if (splits > 1) {
+        kchunk = (K + splits - 1) / splits;
+        kchunk = (kchunk + GBK - 1) / GBK * GBK;
+    }
+    dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, batch * splits);
+    note_launch(); gemm_kernel<LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC,
+                                               batch, splits, kchunk, splitStride);
+}
+
+// ---------------------------------------------------------------------------------------
+// Block reductions
+// ---------------------------------------------------------------------------------------
+FC_DEV double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+FC_DEV double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// Sum over the block; every thread gets the result.  `red` needs blockDim/32 doubles.
+FC_DEV double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) red[0] = t;
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace fc

@@ -1,0 +1,105 @@
+// Launch wrappers of libfc's kernels (host-callable, stream-ordered, no synchronisation).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace fc {
+
+// ---- k_linalg.cu ---------------------------------------------------------------------
+size_t jacobi_smem(int cmax);
+void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
+                   const int* dims, int dstride, int cmax, double* ev, long long bsE,
+                   double* V, int ldv, long long bsV);
+void launch_pchol(cudaStream_t st, int batch, const double* M, int ldm, long long bsM,
+                  const int* dims, int dstride, int cmax, double relTol, double* T, int ldt,
+                  long long bsT, int* rank, int rstride);
+void launch_select_tucker(cudaStream_t st, int d, const double* theta, int ldth, const double* tr,
+                          const double* wn2, double epsfac2, int cap, int* r_out,
+                          double* tail2_out, int* live);
+void launch_select_terms(cudaStream_t st, const double* mu, int ldmu, const int* nslice,
+                         const int* nper, int smax, int pmax, const double* core_e, double frac2,
+                         int maxq, int* q_out, double* sigma, int* tslice, int* tidx,
+                         double* dropped);
+
+// ---- k_tensor.cu ---------------------------------------------------------------------
+struct Piece { const double* xi; const double* U[3]; int ld; int K; double scale; };
+
+void launch_build_symbol(cudaStream_t st, int n, int d, const double* lam, const double* tau,
+                         const double* w, const int* mode, int R, double* E, int lde,
+                         long long bsE, double* xi);
+// out columns = normalised columns of the pieces (in order); weights scale*xi*prod norms.
+void launch_concat_normalize(cudaStream_t st, int d, int n, Piece p0, Piece p1, double* U,
+                             int ldo, long long bsU, double* w);
+// Y[:, t] = |w_t| U[:, t] for t < K (batch over modes)
+void launch_scale_cols_abs(cudaStream_t st, int d, int n, int K, const double* U, int ldu,
+                           long long bsU, const double* w, double* Y, int ldy, long long bsY);
+// Y[:, (k,j)] = |xa_k xb_j| E[:,k] . Yh[:,j]  (explicit Khatri-Rao columns, K = Ra*S)
+void launch_kr_cols(cudaStream_t st, int d, int n, int Ra, int S, const double* E, int lde,
+                    long long bsE, const double* xa, const double* Yh, int ldy, long long bsY,
+                    const double* xb, int absw, double* Y, int ldo, long long bsO);
+// Y = (U diag|w|) Omega, Omega[k,t] ~ N(0,1) from a counter-based hash (seed, mode, k, t)
+void launch_sketch_dense(cudaStream_t st, int d, int n, int K, int c, const double* U, int ldu,
+                         long long bsU, const double* w, unsigned long long seed, double* Y,
+                         int ldy, long long bsY);
+// Y = (E diag|xa| Oa) . (Yh diag|xb| Ob) with Gaussian Oa (Ra x c), Ob (S x c)
+void launch_sketch_kr(cudaStream_t st, int d, int n, int Ra, int S, int c, const double* E,
+                      int lde, long long bsE, const double* xa, const double* Yh, int ldy,
+                      long long bsY, const double* xb, unsigned long long seed, double* Y,
+                      int ldo, long long bsO, double* tmp);
+void launch_weighted_energy(cudaStream_t st, int d, int n, int K, const double* U, int ldu,
+                            long long bsU, const double* w, double* tr);
+// Yr = Y - Q P (deflation), then columns of Yr scaled to unit norm (zero if tiny)
+void launch_deflate_normalize(cudaStream_t st, int d, int n, int c, double* Yr, int ld,
+                              long long bs, const double* Yorig, double relTiny);
+// Q[:, off + j] = Qr[:, j] for j < min(cr, c - off), off = c1 (device counts per mode)
+void launch_combine_cols(cudaStream_t st, int d, int n, int c, double* Q, int ld, long long bs,
+                         const double* Qr, const int* c1, const int* cr, int* ctot);
+// per-mode energy: KR: sum_i GE[i,i] * GY[i,i];  dense: sum_k w_k^2 (all modes equal)
+void launch_trace_kr(cudaStream_t st, int d, int n, const double* GE, int lde, long long bsE,
+                     const double* GY, int ldy, long long bsY, double* tr);
+void launch_sumsq(cudaStream_t st, int K, const double* w, double* out, int nout);
+// ||w_a||^2 * ||w_b||^2 (KR weight norm); out[0]
+void launch_kr_wnorm(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,
+                     double* out);
+// stage-2 gather of the canonical terms into X_l (rmax x q, ld rmax) of each mode
+void launch_gather_terms(cudaStream_t st, int d, int rmax, const int* dims_r, const int* q,
+                         int qmax, const double* sigma, const int* tslice, const int* tidx,
+                         const double* core, int ldcore, const double* W3, int ldw3,
+                         const double* Vs, int ldvs, long long bsVs, double* X, int ldx,
+                         long long bsX);
+// out[0] = sum_{k<Rx, j<Ry} xi_k eta_j prod_l M_l[k,j]
+void launch_inner_reduce(cudaStream_t st, int d, int Rx, int Ry, const double* xi,
+                         const double* eta, const double* M, int ldm, long long bsM, double* out);
+void launch_to_full(cudaStream_t st, int d, int n, int R, const double* xi, const double* U0,
+                    const double* U1, const double* U2, int ld, double* dense);
+// u_hat[i] /= g(rho_i) (full-format eigenbasis solve)
+void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double alpha,
+                       double beta, double gamma, double* x);
+void launch_fill(cudaStream_t st, double* p, size_t count, double v);
+void launch_copy_weights(cudaStream_t st, int K, const double* src, double scale, double* dst);
+// w[(k,j)] = xa[k] * xb[j]
+void launch_outer_weights(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,
+                          double* w);
+// sum of squares of a device vector: out = sum x^2 ; and out = ||core||^2 over live sizes
+void launch_core_energy(cudaStream_t st, int d, const double* core, int ldcore, const int* dims,
+                        double* out);
+// dims bookkeeping for stage 2: dims[3] = min(r1, r2) etc.  (see api.cu for layout)
+void launch_stage2_dims(cudaStream_t st, int d, int* dims);
+
+}  // namespace fc
+
+namespace fc {
+// Layout of the per-truncation device dims array (ints).
+enum {
+    D_R = 0,        // [0..2] Tucker ranks r_l after stage 1
+    D_R12 = 3,      // r_0 * r_1 (rows of the core unfolding)
+    D_R3 = 4,       // r_2 (d = 3) or 1 (d = 2)
+    D_NPER = 5,     // min(r_0, r_1): canonical terms per slice
+    D_Q = 6,        // selected canonical rank
+    D_C1 = 8,       // [8..10]  sketch rank after pass 1 (per mode)
+    D_CR = 11,      // [11..13] rank of the deflated remainder
+    D_CT = 14,      // [14..16] combined basis size
+    D_C3 = 17,      // [17..19] rank after the final orthonormalisation
+    D_SIZE = 24
+};
+}  // namespace fc

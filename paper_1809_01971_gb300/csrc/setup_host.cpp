@@ -1,0 +1,291 @@
+// Host-side setup of libfc (cold path, FP64): the 1D spectrum, the exponential-sum
+// quadratures of rho^-s and the least-squares preconditioner fit.  The factor matrices
+// themselves are built on the device from the node lists produced here.
+//
+// Paper: Section 3.2 (eqn:eig_lap), Section 4.2 (eqn:Sinc_quadr_trunc, eqn:Func_of_rho,
+// eqn:Laplace_transf_rhom1), Lemma 4.1 (positive powers), Section 3.3 (preconditioner).
+#include "setup_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace fc {
+
+std::vector<double> spectrum(int n) {
+    // lambda_k = (4/h^2) sin^2(pi k / (2(n+1))), h = 1/(n+1), k = 1..n  (eqn:eig_lap)
+    const double N = n + 1.0;
+    std::vector<double> lam(n);
+    for (int k = 1; k <= n; ++k) {
+        double s = std::sin(M_PI * k / (2.0 * N));
+        lam[k - 1] = 4.0 * N * N * s * s;
+    }
+    return lam;
+}
+
+// Symmetric eigenvalues/vectors of a small dense matrix by cyclic Jacobi (row-major a, m x m).
+static void small_sym_eig(std::vector<double>& a, int m, std::vector<double>& w,
+                          std::vector<double>& v) {
+    v.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) v[(size_t)i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) off += a[(size_t)p * m + q] * a[(size_t)p * m + q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                double apq = a[(size_t)p * m + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = a[(size_t)p * m + p], aqq = a[(size_t)q * m + q];
+                double th = (aqq - app) / (2.0 * apq);
+                double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < m; ++k) {  // columns p, q
+                    double akp = a[(size_t)k * m + p], akq = a[(size_t)k * m + q];
+                    a[(size_t)k * m + p] = c * akp - s * akq;
+                    a[(size_t)k * m + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {  // rows p, q
+                    double apk = a[(size_t)p * m + k], aqk = a[(size_t)q * m + k];
+                    a[(size_t)p * m + k] = c * apk - s * aqk;
+                    a[(size_t)q * m + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    double vkp = v[(size_t)k * m + p], vkq = v[(size_t)k * m + q];
+                    v[(size_t)k * m + p] = c * vkp - s * vkq;
+                    v[(size_t)k * m + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    w.resize(m);
+    for (int i = 0; i < m; ++i) w[i] = a[(size_t)i * m + i];
+}
+
+// m-point Gauss rule of the positive discrete measure sum_k c_k delta(t - t_k):
+// Stieltjes three-term recurrence on the support points, then the eigen-decomposition of
+// the Jacobi matrix (Golub-Welsch).
+static void gauss_rule(const std::vector<double>& t, const std::vector<double>& c, int m,
+                       std::vector<double>& nodes, std::vector<double>& weights) {
+    const size_t K = t.size();
+    double scale = 0.0, mu0 = 0.0;
+    for (size_t k = 0; k < K; ++k) { scale = std::max(scale, t[k]); mu0 += c[k]; }
+    std::vector<double> x(K), p(K, 1.0), pprev(K, 0.0), pnext(K);
+    for (size_t k = 0; k < K; ++k) x[k] = t[k] / scale;
+    std::vector<double> al(m, 0.0), be(m, 0.0);
+    double normPrev = 1.0;
+    for (int j = 0; j < m; ++j) {
+        double nrm = 0.0, xn = 0.0;
+        for (size_t k = 0; k < K; ++k) { nrm += c[k] * p[k] * p[k]; xn += c[k] * x[k] * p[k] * p[k]; }
+        al[j] = xn / nrm;
+        if (j > 0) be[j] = nrm / normPrev;
+        for (size_t k = 0; k < K; ++k)
+            pnext[k] = (x[k] - al[j]) * p[k] - (j > 0 ? be[j] * pprev[k] : 0.0);
+        pprev.swap(p);
+        p.swap(pnext);
+        normPrev = nrm;
+    }
+    std::vector<double> J((size_t)m * m, 0.0), w, v;
+    for (int i = 0; i < m; ++i) {
+        J[(size_t)i * m + i] = al[i];
+        if (i + 1 < m) {
+            double e = std::sqrt(be[i + 1]);
+            J[(size_t)i * m + i + 1] = e;
+            J[(size_t)(i + 1) * m + i] = e;
+        }
+    }
+    small_sym_eig(J, m, w, v);
+    nodes.resize(m);
+    weights.resize(m);
+    for (int i = 0; i < m; ++i) {
+        nodes[i] = w[i] * scale;
+        weights[i] = mu0 * v[i] * v[i];   // first component of eigenvector i (row 0)
+    }
+}
+
+ExpSum exp_sum(double s, double B, double delta, double s0) {
+    // rho^-s = Gamma(s)^-1 int_R exp(s u - rho e^u) du  (Laplace transform with t = e^u),
+    // trapezoid rule with step h (eqn:Sinc_quadr_trunc); see the readings in the header.
+    ExpSum out;
+    if (!(s > 0.0) || !(B >= 1.0) || !(delta > 0.0)) return out;
+    const double h = M_PI * M_PI / (std::log(1.0 / delta) + 3.0);
+    int m = 1;
+    {
+        // smallest m with s0^(2m)/(2m)! <= delta/100
+        auto term = [&](int mm) { return std::exp(2 * mm * std::log(s0) - std::lgamma(2.0 * mm + 1.0)); };
+        while (term(m) > delta / 100.0 && m < 40) ++m;
+    }
+    const double gs = std::tgamma(s);
+    const long k0 = (long)std::floor(std::log(s0 / B) / h);
+    const long L = (long)std::ceil(46.0 / (s * h));
+    std::vector<double> tt, ct;
+    for (long k = k0 - L; k < k0; ++k) {
+        double u = k * h;
+        tt.push_back(std::exp(u));
+        ct.push_back(h * std::exp(s * u) / gs);
+    }
+    std::vector<double> tg, cg;
+    gauss_rule(tt, ct, m, tg, cg);
+    out.t = tg;
+    out.c = cg;
+    for (long k = k0;; ++k) {
+        double u = k * h;
+        double t = std::exp(u);
+        double c = h * std::exp(s * u) / gs;
+        double r = std::min(std::max(1.0, s / t), B);
+        double contrib = c * std::exp(-t * r) * std::pow(r, s);
+        if (u > 0.0 && contrib < delta / 20.0) break;
+        out.t.push_back(t);
+        out.c.push_back(c);
+        if (out.t.size() > 4000) break;
+    }
+    return out;
+}
+
+double g_exact(double rho, double alpha, double beta, double gamma) {
+    return beta * beta * std::pow(rho, -alpha) + gamma * std::pow(rho, alpha);
+}
+
+bool build_control_nodes(int n, int d, double alpha, double beta, double gamma, double delta,
+                         SymbolNodes& out) {
+    std::vector<double> lam = spectrum(n);
+    const double rmin = d * lam[0], rmax = d * lam[n - 1];
+    const double B = rmax / rmin;
+    out = SymbolNodes();
+    out.rho_min = rmin;
+    out.rho_max = rmax;
+    ExpSum em = exp_sum(alpha, B, delta, 0.5);
+    if (em.t.empty()) return false;
+    for (size_t k = 0; k < em.t.size(); ++k) {
+        out.tau.push_back(em.t[k] / rmin);
+        out.w.push_back(beta * beta * em.c[k] * std::pow(rmin, -alpha));
+        out.mode.push_back(-1);
+    }
+    out.r_minus = (int)em.t.size();
+    if (alpha < 1.0) {
+        ExpSum ep = exp_sum(1.0 - alpha, B, delta, 0.5);
+        if (ep.t.empty()) return false;
+        for (size_t k = 0; k < ep.t.size(); ++k)
+            for (int m = 0; m < d; ++m) {
+                out.tau.push_back(ep.t[k] / rmin);
+                out.w.push_back(gamma * ep.c[k] * std::pow(rmin, alpha - 1.0));
+                out.mode.push_back(m);
+            }
+        out.r_plus = (int)ep.t.size();
+        // accuracy on a geometric rho grid: separable sums evaluated at rho = sum of lambdas
+        double err = 0.0;
+        const int G = 2000;
+        for (int i = 0; i < G; ++i) {
+            double rho = rmin * std::pow(B, i / (G - 1.0));
+            double sm = 0.0, sp = 0.0;
+            for (size_t k = 0; k < em.t.size(); ++k) sm += em.c[k] * std::exp(-em.t[k] * rho / rmin);
+            for (size_t k = 0; k < ep.t.size(); ++k) sp += ep.c[k] * std::exp(-ep.t[k] * rho / rmin);
+            double g = beta * beta * std::pow(rmin, -alpha) * sm + gamma * rho * std::pow(rmin, alpha - 1.0) * sp;
+            err = std::max(err, std::fabs(g / g_exact(rho, alpha, beta, gamma) - 1.0));
+        }
+        out.err = err;
+    } else {
+        for (int m = 0; m < d; ++m) {
+            out.tau.push_back(0.0);
+            out.w.push_back(gamma);
+            out.mode.push_back(m);
+        }
+        out.r_plus = 0;
+        double err = 0.0;
+        const int G = 2000;
+        for (int i = 0; i < G; ++i) {
+            double rho = rmin * std::pow(B, i / (G - 1.0));
+            double sm = 0.0;
+            for (size_t k = 0; k < em.t.size(); ++k) sm += em.c[k] * std::exp(-em.t[k] * rho / rmin);
+            double g = beta * beta * std::pow(rmin, -alpha) * sm + gamma * rho;
+            err = std::max(err, std::fabs(g / g_exact(rho, alpha, beta, gamma) - 1.0));
+        }
+        out.err = err;
+    }
+    return true;
+}
+
+// Least squares min ||A x - b|| (A is m x k column-major, m >= k) by Householder QR.
+static bool lstsq(std::vector<double> A, int m, int k, std::vector<double> b, std::vector<double>& x) {
+    std::vector<double> tau(k);
+    for (int j = 0; j < k; ++j) {
+        double nrm = 0.0;
+        for (int i = j; i < m; ++i) nrm += A[i + (size_t)j * m] * A[i + (size_t)j * m];
+        nrm = std::sqrt(nrm);
+        if (nrm == 0.0) return false;
+        double a0 = A[j + (size_t)j * m];
+        double beta = (a0 >= 0) ? -nrm : nrm;
+        double v0 = a0 - beta;
+        for (int i = j + 1; i < m; ++i) A[i + (size_t)j * m] /= v0;
+        tau[j] = (beta - a0) / beta;
+        A[j + (size_t)j * m] = beta;
+        // apply H = I - tau v v^T (v0 = 1) to the remaining columns and to b
+        for (int c = j + 1; c <= k; ++c) {
+            double* col = (c < k) ? &A[(size_t)c * m] : b.data();
+            double s = col[j];
+            for (int i = j + 1; i < m; ++i) s += A[i + (size_t)j * m] * col[i];
+            s *= tau[j];
+            col[j] -= s;
+            for (int i = j + 1; i < m; ++i) col[i] -= s * A[i + (size_t)j * m];
+        }
+    }
+    x.assign(k, 0.0);
+    for (int j = k - 1; j >= 0; --j) {
+        double s = b[j];
+        for (int c = j + 1; c < k; ++c) s -= A[j + (size_t)c * m] * x[c];
+        x[j] = s / A[j + (size_t)j * m];
+    }
+    return true;
+}
+
+bool build_precond_nodes(int n, int d, double alpha, double beta, double gamma, int rank,
+                         SymbolNodes& out) {
+    // Fit p(rho) = sum_k w_k exp(-tau_k rho) to 1/g(rho) by least squares of p*g - 1 on a
+    // geometric grid of [rho_min, rho_max], nodes tau_k geometric in
+    // [0.2/rho_max, 20/rho_min]; columns scaled to unit norm before the solve.
+    std::vector<double> lam = spectrum(n);
+    const double rmin = d * lam[0], rmax = d * lam[n - 1];
+    out = SymbolNodes();
+    out.rho_min = rmin;
+    out.rho_max = rmax;
+    if (rank < 1) return false;
+    const int G = 3000;
+    std::vector<double> tau(rank), rho(G), g(G);
+    const double lt0 = std::log(0.2 / rmax), lt1 = std::log(20.0 / rmin);
+    for (int k = 0; k < rank; ++k) tau[k] = std::exp(rank == 1 ? lt0 : lt0 + (lt1 - lt0) * k / (rank - 1.0));
+    const double lr0 = std::log(rmin), lr1 = std::log(rmax);
+    for (int i = 0; i < G; ++i) {
+        rho[i] = std::exp(lr0 + (lr1 - lr0) * i / (G - 1.0));
+        g[i] = g_exact(rho[i], alpha, beta, gamma);
+    }
+    std::vector<double> A((size_t)G * rank), cn(rank), b(G, 1.0), w;
+    for (int k = 0; k < rank; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < G; ++i) {
+            double v = g[i] * std::exp(-rho[i] * tau[k]);
+            A[i + (size_t)k * G] = v;
+            s += v * v;
+        }
+        cn[k] = std::sqrt(s);
+        for (int i = 0; i < G; ++i) A[i + (size_t)k * G] /= cn[k];
+    }
+    if (!lstsq(A, G, rank, b, w)) return false;
+    double err = 0.0;
+    for (int k = 0; k < rank; ++k) w[k] /= cn[k];
+    for (int i = 0; i < G; ++i) {
+        double p = 0.0;
+        for (int k = 0; k < rank; ++k) p += w[k] * std::exp(-rho[i] * tau[k]);
+        if (!(p > 0.0)) return false;
+        err = std::max(err, std::fabs(p * g[i] - 1.0));
+    }
+    for (int k = 0; k < rank; ++k) {
+        out.tau.push_back(tau[k]);
+        out.w.push_back(w[k]);
+        out.mode.push_back(-1);
+    }
+    out.r_minus = rank;
+    out.err = err;
+    return true;
+}
+
+}  // namespace fc

@@ -1,0 +1,294 @@
+"""Thin Python binding of libfc (ctypes): argument marshalling only.
+
+Every entry point of ``include/fc.h`` has a function of the same name here; each one
+converts its arguments to the C types, calls the library and raises :class:`FCError`
+on a non-zero status.  All arithmetic runs in the CUDA library.  PyTorch supplies the
+device memory (factor matrices, weights, workspace) and the current CUDA stream.
+
+The library must have been built (``python -m paper_1809_01971_gb300.build``); loading
+fails loudly otherwise.  There is no CPU fallback.
+
+A canonical (CP) tensor (Section 5, eqn:CP_form of the paper)
+    T = sum_{r < rank} xi[r] U_1[:, r] (x) ... (x) U_d[:, r]
+is held by :class:`CP`: ``xi`` of shape (cap,) and ``U`` of shape (d, cap, ld), FP64,
+so ``U[l, r, :n]`` is column r of the column-major n x cap factor matrix U_l.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfc.so")
+
+FC_OK = 0
+FC_EINVAL = -1
+FC_ERANK = -2
+FC_ENOCONV = -3
+FC_EBREAKDOWN = -4
+FC_ENAN = -5
+FC_ECUDA = -6
+FC_EWORKSPACE = -7
+FC_ESETUP = -8
+
+
+class fc_cp(C.Structure):
+    _fields_ = [("d", C.c_int), ("n", C.c_int), ("rank", C.c_int), ("cap", C.c_int),
+                ("ld", C.c_int), ("xi", C.c_void_p), ("U", C.c_void_p * 3)]
+
+
+class fc_setup_opts(C.Structure):
+    _fields_ = [("delta_sym", C.c_double), ("precond_rank", C.c_int), ("max_rank", C.c_int),
+                ("max_tucker", C.c_int), ("max_input_rank", C.c_int)]
+
+
+class fc_setup_info(C.Structure):
+    _fields_ = [("n", C.c_int), ("d", C.c_int), ("rank_symbol", C.c_int),
+                ("rank_minus", C.c_int), ("rank_plus", C.c_int), ("rank_precond", C.c_int),
+                ("rho_min", C.c_double), ("rho_max", C.c_double), ("sym_err", C.c_double),
+                ("pc_err", C.c_double), ("workspace_bytes", C.c_size_t)]
+
+
+class fc_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("eps", C.c_double), ("kmax", C.c_int),
+                ("max_rank", C.c_int)]
+
+
+class fc_solve_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("relres", C.c_double),
+                ("rank_x", C.c_int), ("max_rank_seen", C.c_int), ("trunc_calls", C.c_int),
+                ("history", C.c_double * 128)]
+
+
+class FCError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn}: {msg} ({code})")
+        self.code = code
+
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    """Load libfc.so (built in-tree); raises if it is missing."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfc.so not built: {LIB_PATH} missing; run "
+                               "python -m paper_1809_01971_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        P, I, D, V = C.c_void_p, C.c_int, C.c_double, C.c_void_p
+        cp_p = C.POINTER(fc_cp)
+        sig = {
+            "fc_setup": (I, [I, I, D, D, D, D, C.POINTER(fc_setup_opts), C.POINTER(P)]),
+            "fc_get_info": (I, [P, C.POINTER(fc_setup_info)]),
+            "fc_workspace_size": (I, [P, C.POINTER(C.c_size_t)]),
+            "fc_set_workspace": (I, [P, V, C.c_size_t]),
+            "fc_get_symbol": (I, [P, I, cp_p, V]),
+            "fc_apply": (I, [P, cp_p, cp_p, V]),
+            "fc_precond": (I, [P, cp_p, cp_p, V]),
+            "fc_truncate": (I, [P, cp_p, D, I, I, cp_p, V]),
+            "fc_inner": (I, [P, cp_p, cp_p, C.POINTER(D), V]),
+            "fc_solve": (I, [P, cp_p, cp_p, C.POINTER(fc_solve_opts), C.POINTER(fc_solve_info), V]),
+            "fc_to_full": (I, [P, cp_p, V, V]),
+            "fc_full_solve": (I, [P, V, V, V, V]),
+            "fc_destroy": (None, [P]),
+            "fc_strerror": (C.c_char_p, [I]),
+            "fc_last_cuda_error": (C.c_char_p, []),
+            "fc_launch_count": (C.c_ulonglong, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(fn: str, rc: int) -> int:
+    if rc != FC_OK:
+        L = lib()
+        msg = L.fc_strerror(rc).decode()
+        if rc == FC_ECUDA:
+            msg += ": " + L.fc_last_cuda_error().decode()
+        raise FCError(fn, rc, msg)
+    return rc
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class CP:
+    """Device CP tensor with capacity ``cap`` (weights and factor matrices in FP64)."""
+
+    def __init__(self, d: int, n: int, cap: int, device="cuda", ld: Optional[int] = None):
+        self.d, self.n, self.cap = d, n, cap
+        self.ld = ld if ld is not None else n
+        self.rank = 0
+        self.xi = torch.zeros(max(cap, 1), dtype=torch.float64, device=device)
+        self.U = torch.zeros(d, max(cap, 1), self.ld, dtype=torch.float64, device=device)
+
+    @classmethod
+    def from_factors(cls, xi, U, cap: Optional[int] = None, device="cuda", ld=None) -> "CP":
+        """From weights (R,) and d factor matrices (n, R) (numpy or torch, host or device)."""
+        xi = torch.as_tensor(xi, dtype=torch.float64)
+        d = len(U)
+        n = int(U[0].shape[0])
+        R = int(xi.shape[0])
+        t = cls(d, n, cap if cap is not None else R, device=device, ld=ld)
+        if R > t.cap:
+            raise ValueError("rank exceeds capacity")
+        t.xi[:R].copy_(xi)
+        for l in range(d):
+            t.U[l, :R, :n].copy_(torch.as_tensor(U[l], dtype=torch.float64).T)
+        t.rank = R
+        return t
+
+    def factors(self):
+        """(xi, [U_l]) on the host as numpy arrays, U_l of shape (n, rank)."""
+        R = self.rank
+        xi = self.xi[:R].detach().cpu().numpy().copy()
+        U = [self.U[l, :R, :self.n].detach().cpu().numpy().T.copy() for l in range(self.d)]
+        return xi, U
+
+    def desc(self) -> fc_cp:
+        c = fc_cp()
+        c.d, c.n, c.rank, c.cap, c.ld = self.d, self.n, self.rank, self.cap, self.ld
+        c.xi = self.xi.data_ptr()
+        base = self.U.data_ptr()
+        stride = self.U.stride(0) * 8
+        for l in range(3):
+            c.U[l] = base + (l if l < self.d else 0) * stride
+        return c
+
+
+class Handle:
+    """A set-up problem (fc_setup) with its torch-allocated workspace bound."""
+
+    def __init__(self, ptr: int, device):
+        self.ptr = C.c_void_p(ptr)
+        info = fc_setup_info()
+        _check("fc_get_info", lib().fc_get_info(self.ptr, C.byref(info)))
+        self.info = info
+        nbytes = C.c_size_t()
+        _check("fc_workspace_size", lib().fc_workspace_size(self.ptr, C.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        _check("fc_set_workspace", lib().fc_set_workspace(self.ptr, C.c_void_p(aligned), nbytes.value))
+
+    @property
+    def n(self):
+        return self.info.n
+
+    @property
+    def d(self):
+        return self.info.d
+
+    def destroy(self):
+        if self.ptr:
+            lib().fc_destroy(self.ptr)
+            self.ptr = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fc_setup(n, d, alpha, beta, gamma, eps, delta_sym=0.0, precond_rank=0, max_rank=0,
+             max_tucker=0, max_input_rank=0, device="cuda") -> Handle:
+    o = fc_setup_opts(delta_sym, precond_rank, max_rank, max_tucker, max_input_rank)
+    out = C.c_void_p()
+    _check("fc_setup", lib().fc_setup(int(n), int(d), float(alpha), float(beta), float(gamma),
+                                      float(eps), C.byref(o), C.byref(out)))
+    return Handle(out.value, device)
+
+
+def fc_get_symbol(h: Handle, which: int, out: CP, stream=None) -> CP:
+    c = out.desc()
+    _check("fc_get_symbol", lib().fc_get_symbol(h.ptr, which, C.byref(c), _stream(stream)))
+    out.rank = c.rank
+    return out
+
+
+def _apply(fn: str, h: Handle, x: CP, y: CP, stream) -> CP:
+    cx, cy = x.desc(), y.desc()
+    rc = getattr(lib(), fn)(h.ptr, C.byref(cx), C.byref(cy), _stream(stream))
+    y.rank = cy.rank
+    _check(fn, rc)
+    return y
+
+
+def fc_apply(h: Handle, x: CP, y: CP, stream=None) -> CP:
+    return _apply("fc_apply", h, x, y, stream)
+
+
+def fc_precond(h: Handle, x: CP, y: CP, stream=None) -> CP:
+    return _apply("fc_precond", h, x, y, stream)
+
+
+def fc_truncate(h: Handle, x: CP, eps: float, max_rank: int, y: CP, normalize: bool = True,
+                stream=None) -> CP:
+    cx, cy = x.desc(), y.desc()
+    rc = lib().fc_truncate(h.ptr, C.byref(cx), float(eps), int(max_rank), 1 if normalize else 0,
+                           C.byref(cy), _stream(stream))
+    y.rank = cy.rank
+    _check("fc_truncate", rc)
+    return y
+
+
+def fc_inner(h: Handle, x: CP, y: CP, stream=None) -> float:
+    out = C.c_double()
+    _check("fc_inner", lib().fc_inner(h.ptr, C.byref(x.desc()), C.byref(y.desc()), C.byref(out),
+                                      _stream(stream)))
+    return out.value
+
+
+def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0, stream=None,
+             raise_on_fail: bool = True) -> fc_solve_info:
+    o = fc_solve_opts(float(tol), float(eps), int(kmax), int(max_rank))
+    info = fc_solve_info()
+    cr, cu = rhs.desc(), u.desc()
+    rc = lib().fc_solve(h.ptr, C.byref(cr), C.byref(cu), C.byref(o), C.byref(info), _stream(stream))
+    u.rank = cu.rank
+    if raise_on_fail or rc not in (FC_ENOCONV, FC_EBREAKDOWN, FC_ENAN):
+        _check("fc_solve", rc)
+    return info
+
+
+def fc_to_full(h: Handle, x: CP, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Full n^d array; returned with shape (n,)*d in numpy axis order (i_1 is axis 0)."""
+    n, d = h.n, h.d
+    if out is None:
+        out = torch.empty(n ** d, dtype=torch.float64, device=x.xi.device)
+    _check("fc_to_full", lib().fc_to_full(h.ptr, C.byref(x.desc()), C.c_void_p(out.data_ptr()),
+                                          _stream(stream)))
+    # column-major with i_1 fastest -> numpy axis order reversed
+    return out.view(*([n] * d)).permute(*reversed(range(d)))
+
+
+def fc_launch_count() -> int:
+    """Kernels libfc has launched in this process so far."""
+    return int(lib().fc_launch_count())
+
+
+def fc_full_solve(h: Handle, rhs: torch.Tensor, u: torch.Tensor, tmp: torch.Tensor,
+                  stream=None) -> torch.Tensor:
+    """rhs, u, tmp: contiguous device arrays of n^d doubles, column-major (i_1 fastest)."""
+    for t in (rhs, u, tmp):
+        if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != h.n ** h.d:
+            raise ValueError("full arrays must be contiguous float64 with n^d elements")
+    _check("fc_full_solve", lib().fc_full_solve(h.ptr, C.c_void_p(rhs.data_ptr()),
+                                                C.c_void_p(u.data_ptr()), C.c_void_p(tmp.data_ptr()),
+                                                _stream(stream)))
+    return u

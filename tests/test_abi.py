@@ -1,0 +1,49 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point that
+include/fc.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fc_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_declared_symbols():
+    from paper_1809_01971_gb300 import build, fc
+    if not os.path.exists(fc.LIB_PATH):
+        build.build()
+    lib = ctypes.CDLL(fc.LIB_PATH)
+    names = _declared()
+    assert {"fc_setup", "fc_apply", "fc_precond", "fc_truncate", "fc_solve", "fc_inner"} <= names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    # every declared name is bound by the Python binding with the same name
+    fc.lib()
+    assert all(hasattr(fc.lib(), n) for n in names)
+
+
+def test_strerror_is_host_only():
+    from paper_1809_01971_gb300 import fc
+    L = fc.lib()
+    assert L.fc_strerror(fc.FC_ERANK).decode() == "rank capacity exceeded"
+    assert L.fc_strerror(12345).decode() == "unknown error"
+
+
+def test_setup_rejects_bad_parameters_without_touching_the_gpu():
+    """Argument checks run before any CUDA call (paper range 0 < alpha <= 1, d in {2,3})."""
+    from paper_1809_01971_gb300 import fc
+    L = fc.lib()
+    out = ctypes.c_void_p()
+    for args in [(63, 4, 0.5, 1.0, 1e-2, 1e-8), (63, 2, 1.5, 1.0, 1e-2, 1e-8),
+                 (0, 2, 0.5, 1.0, 1e-2, 1e-8), (63, 2, 0.5, -1.0, 1e-2, 1e-8),
+                 (63, 3, 0.5, 1.0, 0.0, 1e-8), (63, 3, 0.5, 1.0, 1e-2, 0.0)]:
+        assert L.fc_setup(*args, None, ctypes.byref(out)) == fc.FC_EINVAL

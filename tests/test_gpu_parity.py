@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Every case runs on seeded synthetic inputs (fc_inputs) at sizes the oracle finishes in
+seconds, with ragged n (not a multiple of the 64-wide GEMM tile) and several tiles.
+Tolerances (relative L2 of the represented full tensors unless stated):
+  * exact-arithmetic steps (DST-I mat-vec, inner product, full expansion, full-format
+    solve): 1e-12, the FP64 rounding level of O(n) sums of O(1) terms;
+  * symbol against the exact g(rho): 1e-9 (setup targets 1e-10 on a rho grid);
+  * truncation: c * eps * ||T|| with c from the split of eps over the RHOSVD stages;
+  * CP-PCG solve against the oracle's full solution: max(eps, 1e-8) scaled by the
+    operator's conditioning as stated per test.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import fc_inputs as fi
+from oracle import cp, full, quadrature as q
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import paper_1809_01971_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def sym_obj(fc, h, which):
+    s = fc.CP(h.d, h.n, h.info.rank_symbol if which == 0 else h.info.rank_precond)
+    fc.fc_get_symbol(h, which, s)
+    xi, U = s.factors()
+    return q.Symbol(xi, U, None, "gpu")
+
+
+def gpu_full(fc, h, X):
+    return fc.fc_to_full(h, X).cpu().numpy()
+
+
+@pytest.mark.parametrize("n,d,alpha,gamma_", [(15, 2, 0.5, 1e-2), (63, 2, 0.5, 1e-2),
+                                             (15, 3, 0.25, 1e-1), (37, 3, 0.75, 1e-3),
+                                             (20, 3, 1.0, 1e-2)])
+def test_symbol_matches_exact_g(fc, n, d, alpha, gamma_):
+    h = fc.fc_setup(n, d, alpha, 1.0, gamma_, 1e-8)
+    assert h.info.sym_err < 1e-9
+    s = sym_obj(fc, h, 0)
+    G = cp.to_full((s.xi, s.U))
+    lams = [q.eigenvalues(n)] * d if hasattr(q, "eigenvalues") else None
+    from oracle.spectrum import eigenvalues
+    rho = q.rho_full([eigenvalues(n)] * d)
+    g = q.g_control(rho, alpha, 1.0, gamma_)
+    err = float(np.max(np.abs(G / g - 1.0)))
+    print(f"n={n} d={d} a={alpha} RA={h.info.rank_symbol} symbol max rel err {err:.3e}")
+    assert err < 1e-9
+    del lams
+
+
+@pytest.mark.parametrize("n,d,alpha,gamma_", [(31, 2, 0.5, 1e-2), (25, 3, 0.25, 1e-3)])
+def test_precond_symbol_is_positive_and_close_to_inverse(fc, n, d, alpha, gamma_):
+    h = fc.fc_setup(n, d, alpha, 1.0, gamma_, 1e-8)
+    s = sym_obj(fc, h, 1)
+    P = cp.to_full((s.xi, s.U))
+    from oracle.spectrum import eigenvalues
+    rho = q.rho_full([eigenvalues(n)] * d)
+    g = q.g_control(rho, alpha, 1.0, gamma_)
+    assert np.all(P > 0)
+    dev = float(np.max(np.abs(P * g - 1.0)))
+    print(f"precond rank {h.info.rank_precond} max|p g - 1| = {dev:.3e} (setup grid {h.info.pc_err:.3e})")
+    assert dev <= 0.5
+
+
+@pytest.mark.parametrize("n,d,S", [(37, 2, 3), (70, 2, 5), (29, 3, 4), (66, 3, 2)])
+@pytest.mark.parametrize("which", [0, 1])
+def test_apply_and_precond_match_oracle_matvec(fc, n, d, S, which):
+    """fc_apply / fc_precond equal the oracle's mode-wise mat-vec with the same symbol
+    (eqn:Lap2DtimesX / eqn:Lap3DtimesX) to rounding, and the exact operator to 1e-9."""
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, 1e-8)
+    X = fi.random_cp(n, d, S, seed=fi.seed_for(7, n + S))
+    Xg = fc.CP.from_factors(*X)
+    R = h.info.rank_symbol if which == 0 else h.info.rank_precond
+    Y = fc.CP(d, n, R * S)
+    (fc.fc_apply if which == 0 else fc.fc_precond)(h, Xg, Y)
+    assert Y.rank == R * S
+    s = sym_obj(fc, h, which)
+    ref = cp.to_full(cp.apply_symbol(s, X))
+    got = gpu_full(fc, h, Y)
+    e = rel(got, ref)
+    print(f"which={which} n={n} d={d} S={S}: rel err vs oracle mat-vec {e:.3e}")
+    assert e < 1e-12
+    if which == 0:
+        exact = full.apply_full(cp.to_full(X), 0.5, 1.0, 1e-2)
+        assert rel(got, exact) < 1e-9
+
+
+@pytest.mark.parametrize("n,d", [(45, 2), (33, 3), (130, 3)])
+def test_inner_and_to_full_match_oracle(fc, n, d):
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, 1e-8)
+    X = fi.random_cp(n, d, 5, seed=11)
+    Y = fi.random_cp(n, d, 7, seed=12)
+    Xg, Yg = fc.CP.from_factors(*X), fc.CP.from_factors(*Y)
+    v = fc.fc_inner(h, Xg, Yg)
+    ref = cp.inner(X, Y)
+    scale = cp.norm(X) * cp.norm(Y)
+    assert abs(v - ref) <= 1e-13 * scale
+    assert rel(gpu_full(fc, h, Xg), cp.to_full(X)) < 1e-14
+    empty = fc.CP(d, n, 4)
+    assert fc.fc_inner(h, empty, Xg) == 0.0
+
+
+def _decaying_cp(n, d, R, seed, rate=0.5):
+    xi, U = fi.random_cp(n, d, R, seed)
+    xi = np.abs(xi) * rate ** np.arange(R)
+    return xi, U
+
+
+@pytest.mark.parametrize("n,d,R,eps", [(40, 2, 6, 1e-10), (53, 3, 6, 1e-10), (70, 3, 30, 1e-6),
+                                      (61, 2, 40, 1e-8), (100, 3, 60, 1e-8)])
+def test_truncate_matches_oracle(fc, n, d, R, eps):
+    """trunc (Section 5 RHOSVD / 2D reduced SVD) reproduces the tensor within its eps
+    budget and agrees with the oracle's QR+SVD truncation in full form."""
+    if R <= 6:   # exact low rank, duplicated terms: truncation must be lossless
+        base = fi.random_cp(n, d, 3, seed=21)
+        X = cp.axpy(base, 0.5, base)
+        X = (np.concatenate([X[0][:3], X[0][3:]]), X[1])
+    else:
+        X = _decaying_cp(n, d, R, seed=22)
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, eps, max_rank=32, max_input_rank=max(32, R))
+    Xg = fc.CP.from_factors(*X)
+    Y = fc.CP(d, n, 64)
+    fc.fc_truncate(h, Xg, eps, 32, Y, normalize=True)
+    Xf = cp.to_full(X)
+    Yf = gpu_full(fc, h, Y)
+    from oracle.truncate import truncate
+    ref = truncate(X, eps, 32)
+    Rf = cp.to_full(ref)
+    e_in = rel(Yf, Xf)
+    e_or = rel(Yf, Rf)
+    e_oracle_in = rel(Rf, Xf)
+    print(f"n={n} d={d} R={R} eps={eps:g}: gpu rank {Y.rank} (oracle {len(ref[0])}); "
+          f"|gpu-X|={e_in:.3e} |oracle-X|={e_oracle_in:.3e} |gpu-oracle|={e_or:.3e}")
+    assert Y.rank >= 1
+    assert e_in <= 2.0 * eps + 1e-13
+    assert e_or <= 3.0 * eps + 1e-13
+
+
+@pytest.mark.parametrize("n,d", [(63, 2), (31, 3), (50, 3)])
+def test_full_solve_matches_oracle(fc, n, d):
+    rng = np.random.default_rng(fi.seed_for(8, n))
+    y = fi.gaussians_cp(n, d, 3, rng)
+    b = cp.to_full(y)
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, 1e-8)
+    # column-major (i_1 fastest) = numpy array with reversed axes, C order
+    flat = torch.tensor(np.ascontiguousarray(b.transpose(*reversed(range(d)))).reshape(-1),
+                        device="cuda")
+    u = torch.empty_like(flat)
+    tmp = torch.empty_like(flat)
+    fc.fc_full_solve(h, flat, u, tmp)
+    got = u.cpu().numpy().reshape([n] * d).transpose(*reversed(range(d)))
+    ref = full.solve_full(b, 0.5, 1.0, 1e-2)
+    e = rel(got, ref)
+    print(f"full solve n={n} d={d}: rel err {e:.3e}")
+    assert e < 1e-12
+
+
+@pytest.mark.parametrize("n,modes,alpha,gamma_", [(63, (1, 2, 3), 0.5, 1e-3),
+                                                  (45, (3, 1), 0.25, 1e-1)])
+def test_solve_sine_mode_exact(fc, n, modes, alpha, gamma_):
+    """A grid sine mode is an eigenvector of A (Section 3.2): u = b / g(rho_m) exactly."""
+    d = len(modes)
+    y = fi.sine_cp(n, modes)
+    h = fc.fc_setup(n, d, alpha, 1.0, gamma_, 1e-10)
+    B = fc.CP.from_factors(*y)
+    U = fc.CP(d, n, 32)
+    info = fc.fc_solve(h, B, U, tol=1e-10)
+    lam = [(2 * (n + 1)) ** 2 * math.sin(math.pi * m / (2 * (n + 1))) ** 2 for m in modes]
+    rho = sum(lam)
+    ref = cp.to_full(y) / (rho ** (-alpha) + gamma_ * rho ** alpha)
+    e = rel(gpu_full(fc, h, U), ref)
+    print(f"sine mode {modes}: iters {info.iters} rank {U.rank} rel err {e:.3e}")
+    assert e < 1e-8
+
+
+def _solve_vs_full(fc, prob, tol, eps, max_rank=32):
+    h = fc.fc_setup(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, eps, max_rank=max_rank)
+    B = fc.CP.from_factors(*prob.rhs())
+    U = fc.CP(prob.d, prob.n, max_rank)
+    info = fc.fc_solve(h, B, U, tol=tol, eps=eps)
+    ref = full.solve_full(cp.to_full(prob.rhs()), prob.alpha, prob.beta, prob.gamma)
+    e = rel(gpu_full(fc, h, U), ref)
+    hist = [info.history[i] for i in range(min(info.iters, 8))]
+    print(f"{prob.label}: iters {info.iters} relres {info.relres:.2e} rank {U.rank} "
+          f"max rank {info.max_rank_seen} err vs full {e:.3e} hist {['%.1e' % x for x in hist]}")
+    return info, e
+
+
+def test_solve_config1_2d(fc):
+    """2D, n=63, alpha=1/2, gamma=1e-2, two Gaussians: CP-PCG vs the full oracle."""
+    prob = fi.config1()
+    info, e = _solve_vs_full(fc, prob, 1e-8, 1e-8)
+    assert info.status == 0
+    assert e < 1e-7
+
+
+@pytest.mark.parametrize("problem", [0, 3, 5])
+def test_solve_config2_3d_n255(fc, problem):
+    """3D, n=255, 4 Gaussians + sine mode: CP-PCG vs the full oracle (16.6M points)."""
+    prob = fi.config2(problem)
+    info, e = _solve_vs_full(fc, prob, 1e-7, 1e-7)
+    assert info.status == 0
+    assert e < 1e-6
