@@ -142,6 +142,15 @@ int fc_precond(fc_handle h, const fc_cp* x, fc_cp* y, void* stream);
 int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int normalize,
                 fc_cp* y, void* stream);
 
+/* y = trunc(F(A) x, eps) as one fused step (the lines S = trunc(fun(P)) and
+ * Z = trunc(precond(R)) of Algorithm 1): which = 0 applies the operator symbol, which = 1 the
+ * preconditioner.  The R_A * x->rank (or R_P * x->rank) Khatri-Rao columns of the mat-vec are
+ * never formed in HBM: the truncation (same rule as fc_truncate with normalize = 0) reads them
+ * implicitly in the eigen-index domain and applies the inverse DST-I only to the r_l Tucker
+ * basis columns (F is orthogonal, Section 3.2).  x->rank <= max_input_rank.  Synchronises. */
+int fc_apply_trunc(fc_handle h, int which, const fc_cp* x, double eps, int max_rank, fc_cp* y,
+                   void* stream);
+
 /* *out_host = <x, y> = sum_{k,j} xi_k eta_j prod_l <x_lk, y_lj> (inner products of
  * Algorithm 1).  Synchronises. */
 int fc_inner(fc_handle h, const fc_cp* x, const fc_cp* y, double* out_host, void* stream);

@@ -630,6 +630,19 @@ int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int norma
     return rc;
 }
 
+int fc_apply_trunc(fc_handle h, int which, const fc_cp* x, double eps, int max_rank, fc_cp* y,
+                   void* stream) {
+    if (!h || !(which == 0 || which == 1) || !check_cp(h, x, false) || !check_cp(h, y, true) ||
+        !(eps >= 0.0) || max_rank < 1)
+        return FC_EINVAL;
+    if (!h->ws) return FC_EWORKSPACE;
+    if (x->rank > h->KIN) { y->rank = x->rank; return FC_ERANK; }
+    CP xc = from_user(x), yc = from_user(y);
+    int rc = kr_trunc(h, (cudaStream_t)stream, xc, which == 1, eps, max_rank, yc);
+    y->rank = yc.rank;
+    return rc;
+}
+
 int fc_inner(fc_handle h, const fc_cp* x, const fc_cp* y, double* out_host, void* stream) {
     if (!h || !out_host || !check_cp(h, x, false) || !check_cp(h, y, false)) return FC_EINVAL;
     if (!h->ws) return FC_EWORKSPACE;

@@ -211,7 +211,13 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
             int p = k; double best = dg[perm[k]];
             for (int i = k + 1; i < c; ++i) if (dg[perm[i]] > best) { best = dg[perm[i]]; p = i; }
             if (!(best > relTol * dmax0) || !(best > 0.0)) rk = k;
-            else { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
+            else if (p != k) {
+                // rows of L are stored by pivot position: move the computed part with the pivot
+                int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+                for (int j = 0; j < k; ++j) {
+                    double x = L[k * SS + j]; L[k * SS + j] = L[p * SS + j]; L[p * SS + j] = x;
+                }
+            }
         }
         __syncthreads();
         if (rk <= k) break;

@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
             "fc_precond": (I, [P, cp_p, cp_p, V]),
             "fc_truncate": (I, [P, cp_p, D, I, I, cp_p, V]),
             "fc_inner": (I, [P, cp_p, cp_p, C.POINTER(D), V]),
+            "fc_apply_trunc": (I, [P, I, cp_p, D, I, cp_p, V]),
             "fc_solve": (I, [P, cp_p, cp_p, C.POINTER(fc_solve_opts), C.POINTER(fc_solve_info), V]),
             "fc_to_full": (I, [P, cp_p, V, V]),
             "fc_full_solve": (I, [P, V, V, V, V]),
@@ -244,6 +245,16 @@ def fc_truncate(h: Handle, x: CP, eps: float, max_rank: int, y: CP, normalize: b
                            C.byref(cy), _stream(stream))
     y.rank = cy.rank
     _check("fc_truncate", rc)
+    return y
+
+
+def fc_apply_trunc(h: Handle, which: int, x: CP, eps: float, max_rank: int, y: CP,
+                   stream=None) -> CP:
+    cx, cy = x.desc(), y.desc()
+    rc = lib().fc_apply_trunc(h.ptr, int(which), C.byref(cx), float(eps), int(max_rank),
+                              C.byref(cy), _stream(stream))
+    y.rank = cy.rank
+    _check("fc_apply_trunc", rc)
     return y
 
 

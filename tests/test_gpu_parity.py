@@ -153,6 +153,45 @@ def test_truncate_matches_oracle(fc, n, d, R, eps):
     assert e_or <= 3.0 * eps + 1e-13
 
 
+@pytest.mark.parametrize("n,d,R,eps", [(80, 3, 100, 1e-8), (57, 2, 90, 1e-9)])
+def test_truncate_sketch_path_matches_oracle(fc, n, d, R, eps):
+    """More terms than the 64-column sketch: the randomised range of the side matrices
+    must still capture every direction above the eps budget."""
+    X = _decaying_cp(n, d, R, seed=23, rate=0.7)
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, eps, max_rank=32, max_input_rank=R)
+    Xg = fc.CP.from_factors(*X)
+    Y = fc.CP(d, n, 64)
+    fc.fc_truncate(h, Xg, eps, 32, Y, normalize=True)
+    from oracle.truncate import truncate
+    ref = truncate(X, eps, 32)
+    Xf, Yf, Rf = cp.to_full(X), gpu_full(fc, h, Y), cp.to_full(ref)
+    print(f"sketch n={n} d={d} R={R}: gpu rank {Y.rank} oracle {len(ref[0])} "
+          f"|gpu-X|={rel(Yf, Xf):.3e} |oracle-X|={rel(Rf, Xf):.3e}")
+    assert rel(Yf, Xf) <= 2.0 * eps + 1e-13
+    assert rel(Yf, Rf) <= 3.0 * eps + 1e-13
+
+
+@pytest.mark.parametrize("n,d,S,which,eps", [(31, 2, 3, 0, 1e-8), (40, 3, 4, 0, 1e-7),
+                                             (40, 3, 4, 1, 1e-7), (64, 3, 8, 0, 1e-6)])
+def test_apply_trunc_matches_oracle(fc, n, d, S, which, eps):
+    """trunc(fun(x)) / trunc(precond(x)) of Algorithm 1 with the Khatri-Rao columns kept
+    implicit, against the oracle's truncation of the explicit mat-vec (normalize=False)."""
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, eps, max_rank=32)
+    X = _decaying_cp(n, d, S, seed=24, rate=0.6)
+    Xg = fc.CP.from_factors(*X)
+    Y = fc.CP(d, n, 32)
+    fc.fc_apply_trunc(h, which, Xg, eps, 32, Y)
+    s = sym_obj(fc, h, which)
+    M = cp.apply_symbol(s, X)
+    from oracle.truncate import truncate
+    ref = truncate(M, eps, 32, normalize=False)
+    Mf, Yf, Rf = cp.to_full(M), gpu_full(fc, h, Y), cp.to_full(ref)
+    print(f"apply_trunc which={which} n={n} d={d} S={S} K={len(M[0])}: gpu rank {Y.rank} "
+          f"oracle {len(ref[0])} |gpu-M|={rel(Yf, Mf):.3e} |oracle-M|={rel(Rf, Mf):.3e}")
+    assert rel(Yf, Mf) <= 2.0 * eps
+    assert rel(Yf, Rf) <= 3.0 * eps
+
+
 @pytest.mark.parametrize("n,d", [(63, 2), (31, 3), (50, 3)])
 def test_full_solve_matches_oracle(fc, n, d):
     rng = np.random.default_rng(fi.seed_for(8, n))
