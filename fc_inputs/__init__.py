@@ -104,7 +104,7 @@ def config2(problem: int) -> Problem:
     s = seed_for(2, problem)
     rng = np.random.default_rng(s)
     y = concat_cp(gaussians_cp(255, 3, 4, rng), sine_cp(255, (1, 2, 3)))
-    return Problem(255, 3, a, 1.0, g, y, eps=1e-7, tol=1e-7, max_rank=32, seed=s,
+    return Problem(255, 3, a, 1.0, g, y, eps=1e-7, tol=1e-7, max_rank=96, seed=s,
                    label=f"3d_n255_a{a}_g{g:g}")
 
 

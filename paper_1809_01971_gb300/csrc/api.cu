@@ -224,18 +224,33 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
             launch_sketch_dense(st, d, n, (int)K, c, dn->U, dn->ld, dn->bs, dn->w, seed, w.Y, n, nC);
     }
     CKL();
-    // three Cholesky-QR passes with diagonal pivoting: Q = orth(Y) (span preserved)
-    double* src = w.Y;
-    double* dst = w.Q;
+    // Orthonormal basis of range(Y) by pivoted Cholesky-QR with one deflation level.
+    // A Cholesky factor of the Gram resolves only directions with sigma / sigma_max above
+    // ~sqrt(relTol) = 3e-8; the directions it drops are recovered from the remainder
+    // Y - Q1 Q1^T Y, which is column-normalised and orthonormalised on its own, then
+    // appended to Q1 and re-orthonormalised (span preserved to ~1e-15 relative).
     const long long CC = (long long)CM * CM;
-    for (int pass = 0; pass < 3; ++pass) {
+    auto cholqr = [&](const double* src, double* dst, int* rk) {
         gemm(st, c, c, n, LdT{src, n, nC}, LdN{src, n, nC}, 1.0, 0.0, w.M, CM, CC, d);
-        launch_pchol(st, d, w.M, CM, CC, nullptr, 0, c, 1e-15, w.Tm, CM, CC, dims + D_C1, 1);
+        launch_pchol(st, d, w.M, CM, CC, nullptr, 0, c, 1e-15, w.Tm, CM, CC, rk, 1);
         gemm(st, n, c, c, LdN{src, n, nC}, LdN{w.Tm, CM, CC}, 1.0, 0.0, dst, n, nC, d);
-        std::swap(src, dst);
-        if (pass == 0) dst = w.Y2;
-    }
-    double* Qb = src;   // orthonormal basis, live columns dims[D_C1 + l]
+    };
+    cholqr(w.Y, w.Q, dims + D_C1);           // Q1 (orthogonal to ~kappa^2 u)
+    cholqr(w.Q, w.Y2, dims + D_C1);          // Q1 re-orthonormalised
+    // remainder tmp = Y - Q1 (Q1^T Y), columns scaled to unit norm (zero if at rounding level)
+    gemm(st, c, c, n, LdT{w.Y2, n, nC}, LdN{w.Y, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+    CK(cudaMemcpyAsync(w.tmp, w.Y, sizeof(double) * d * nC, cudaMemcpyDeviceToDevice, st));
+    gemm(st, n, c, c, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.tmp, n, nC, d);
+    launch_deflate_normalize(st, d, n, c, w.tmp, n, nC, w.Y, 1e-13);
+    cholqr(w.tmp, w.Q, dims + D_CR);         // Q2
+    // Q2 <- Q2 - Q1 (Q1^T Q2), re-orthonormalised
+    gemm(st, c, c, n, LdT{w.Y2, n, nC}, LdN{w.Q, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+    gemm(st, n, c, c, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.Q, n, nC, d);
+    cholqr(w.Q, w.GQ, dims + D_CR);
+    // [Q1 | Q2] and a final pass; live columns of the basis -> dims[D_C1 + l]
+    launch_combine_cols(st, d, n, c, w.Y2, n, nC, w.GQ, dims + D_C1, dims + D_CR, dims + D_CT);
+    cholqr(w.Y2, w.Q, dims + D_C1);
+    double* Qb = w.Q;
     CKL();
     // Rayleigh-Ritz matrix T = Q^T W W^T Q and energy tr = ||W||_F^2
     if (kr) {
