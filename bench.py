@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--problems", type=int, default=6)
+    p.add_argument("--max-err", type=float, default=1e-6,
+                   help="exit status 3 when a solution's error vs the full solve exceeds this")
     return p.parse_args()
 
 
@@ -305,7 +307,7 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-    return 0 if max_err <= 1e-6 else 3
+    return 0 if max_err <= args.max_err else 3
 
 
 if __name__ == "__main__":

@@ -91,13 +91,12 @@ struct fc_ctx {
     // workspace slices
     struct {
         double *Y, *Y2, *Q, *tmp, *M, *Tm, *GY, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *wK;
-        double *corep, *core, *G3, *ev3, *W3, *Srot, *SG, *mus, *Vs, *sigma, *X, *Yh;
+        double *core, *G3, *ev3, *W3, *Srot, *SG, *mus, *Vs, *sigma, *X, *Yh;
         double *scal, *Mi;
         int *dims, *tslice, *tidx;
         CP cat, Xs, Rs, Ps, Zs, Ss;
         double* pinned_dummy;
     } w{};
-    int splits = 1;
     unsigned long long seed = 0x1809019710ull;
     // host pinned scalars for readback
     double* hbuf = nullptr;
@@ -126,7 +125,6 @@ size_t layout(fc_ctx* h, Arena& a) {
     w.Zr = a.d(3 * (size_t)n * RM);
     w.C = a.d(3 * (size_t)std::max(RM, CM) * K);
     w.wK = a.d((size_t)K);
-    w.corep = a.d((size_t)h->splits * RM * RM * RM);
     w.core = a.d((size_t)RM * RM * RM);
     w.G3 = a.d((size_t)RM * RM);
     w.ev3 = a.d((size_t)RM);
@@ -300,21 +298,13 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     CKL();
     // ---- core: B3[(a + r0 b), c] = sum_K w_K C0[a,K] C1[b,K] C2[c,K] ----------------------
     const int RR = RM * RM;
-    int splits = (int)std::min<long long>(h->splits, std::max<long long>(1, K / 128));
-    double* coreOut = (splits > 1) ? w.corep : w.core;
     LdCore A{w.C, w.C + RK, wK, RM, dims + D_R};
     if (d == 3)
-        gemm(st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, RM, 0}, 1.0, 0.0, coreOut, RR, 0, 1,
-             dims + D_R12, dims + D_R3, nullptr, splits, (long long)RR * RM);
+        gemm(st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, RM, 0}, 1.0, 0.0, w.core, RR, 0, 1,
+             dims + D_R12, dims + D_R3, nullptr);
     else
-        gemm(st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, coreOut, RR, 0, 1, dims + D_R12, nullptr,
-             nullptr, splits, (long long)RR * RM);
-    if (splits > 1) {
-        // reduce partials: core = sum_s corep[s]
-        // (use a GEMM with K = 1 and B = ones to sum; rows = RR*RM flattened)
-        gemm(st, RR * RM, 1, 1, LdPart{w.corep, splits, (long long)RR * RM}, LdOnes{}, 1.0, 0.0,
-             w.core, RR * RM);
-    }
+        gemm(st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, w.core, RR, 0, 1, dims + D_R12, nullptr,
+             nullptr);
     CKL();
     launch_core_energy(st, d, w.core, RR, dims, w.scal + 12);
     // mode-3 rotation: G3 = B3^T B3, W3 = eigvecs, Srot = B3 W3
@@ -467,7 +457,6 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     h->QMAX = std::max(h->CAP, h->KIN);
     h->KMAX = std::max<long long>({(long long)h->RA * h->KIN, (long long)h->RP * h->KIN,
                                    2LL * h->CAP, (long long)h->KIN});
-    h->splits = 32;
     // device tables
     const int N = n + 1;
     const int RAm = std::max(h->RA, h->RP);

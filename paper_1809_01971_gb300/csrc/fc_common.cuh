@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <algorithm>
 
 #define FC_DEV __device__ __forceinline__
 
@@ -106,17 +107,20 @@ struct LdSl {     // op = slice : (a, b)
 // ---------------------------------------------------------------------------------------
 // C[b] = alpha * op(A)[b] * op(B)[b] + beta * C[b]   (M x N, inner K), FP64.
 // Sizes can come from device memory (dM/dN/dK non-null) so that one launch covers the
-// largest case and blocks outside the live size return.  Split-K: gridDim.z = batch*splits,
-// split s handles K range [s*kchunk, (s+1)*kchunk) and writes C + s*splitStride (the caller
-// reduces the partials).  Register tile 4x4 per thread, 64x64 block tile, BK = 16.
+// largest case and blocks outside the live size return.  Split-K: gridDim.z = batch*splits;
+// split s handles the K range [s*kchunk, (s+1)*kchunk) and adds alpha * its partial product
+// to C with FP64 atomics (C pre-scaled by beta in a separate launch).  GB300 issues few
+// FP64 FMAs per SM per clock, so a GEMM whose output tiles cannot fill the 152 SMs is
+// split along K until they do.  Register tile 4x4 per thread, 64x64 block tile, BK = 16.
 // ---------------------------------------------------------------------------------------
 constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int kNumSMs = 152;
 
 template <class LA, class LB>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
             LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
-            int batch, int splits, int kchunk, long long splitStride)
+            int batch, int splits, int kchunk)
 {
     __shared__ double As[GBK][GBM + 1];
     __shared__ double Bs[GBK][GBN + 1];
@@ -164,7 +168,7 @@ gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
         }
         __syncthreads();
     }
-    double* Cb = C + zb * bsC + zs * splitStride;
+    double* Cb = C + zb * bsC;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         int gi = m0 + ty + 16 * i;
@@ -174,26 +178,42 @@ gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
             int gj = n0 + tx + 16 * j;
             if (gj >= N) continue;
             double* c = Cb + gi + (long long)gj * ldc;
-            *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+            if (splits > 1) atomicAdd(c, alpha * acc[i][j]);
+            else *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
         }
     }
 }
 
+// C[b][i, j] *= beta (beta == 0: set to 0) over the live M x N (split-K pre-pass).
+__global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN, double beta,
+                                     double* C, int ldc, long long bsC);
+
 template <class LA, class LB>
 inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha, double beta,
                  double* C, int ldc, long long bsC = 0, int batch = 1,
-                 const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr,
-                 int splits = 1, long long splitStride = 0)
+                 const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr)
 {
     if (M <= 0 || N <= 0 || batch <= 0) return;
+    const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
+    int splits = 1;
+    if (tiles < 2 * kNumSMs && K >= 256) {
+        long long want = (2 * kNumSMs + tiles - 1) / tiles;
+        long long most = (K + 127) / 128;          // at least 128 of K per split
+        splits = (int)std::min<long long>(std::min(want, most), 64);
+    }
     int kchunk = K;
     if (splits > 1) {
         kchunk = (K + splits - 1) / splits;
         kchunk = (kchunk + GBK - 1) / GBK * GBK;
+        splits = (K + kchunk - 1) / kchunk;
+    }
+    if (splits > 1 && beta != 1.0) {
+        dim3 g((M + 255) / 256, N, batch);
+        note_launch(); gemm_prescale_kernel<<<g, 256, 0, st>>>(M, N, dM, dN, beta, C, ldc, bsC);
     }
     dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, batch * splits);
     note_launch(); gemm_kernel<LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC,
-                                               batch, splits, kchunk, splitStride);
+                                               batch, splits, kchunk);
 }
 
 // ---------------------------------------------------------------------------------------

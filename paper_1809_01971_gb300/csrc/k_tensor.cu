@@ -7,6 +7,17 @@
 
 namespace fc {
 
+__global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN, double beta,
+                                     double* C, int ldc, long long bsC)
+{
+    if (dM) M = min(M, *dM);
+    if (dN) N = min(N, *dN);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= M || j >= N) return;
+    double* c = C + blockIdx.z * bsC + i + (long long)j * ldc;
+    *c = (beta == 0.0) ? 0.0 : beta * (*c);
+}
+
 // ---------------------------------------------------------------------------------------
 // Symbol factors (eqn:Func_of_rho, Lemma 4.1): term k, mode l:
 //   E_l[i, k] = exp(-tau_k lambda_i) * (l == mode_k ? lambda_i : 1),

@@ -212,11 +212,18 @@ def test_apply_trunc_matches_oracle(fc, n, d, S, which, eps):
     from oracle.truncate import truncate
     ref = truncate(M, eps, 1024, normalize=False)
     Mf, Yf, Rf = cp.to_full(M), gpu_full(fc, h, Y), cp.to_full(ref)
+    # the RHOSVD budget is set by the weight norm ||xi||_2 of the (non-orthogonal)
+    # Khatri-Rao representation, which exceeds ||M||_F: bound the absolute error by it
+    wn = float(np.linalg.norm(M[0]))
+    ag, ao, agr = (np.linalg.norm(Yf - Mf) / wn, np.linalg.norm(Rf - Mf) / wn,
+                   np.linalg.norm(Yf - Rf) / wn)
     print(f"apply_trunc which={which} n={n} d={d} S={S} K={len(M[0])}: gpu rank {Y.rank} "
-          f"oracle {len(ref[0])} |gpu-M|={rel(Yf, Mf):.3e} |oracle-M|={rel(Rf, Mf):.3e}")
+          f"oracle {len(ref[0])} |gpu-M|/|xi|={ag:.3e} |oracle-M|/|xi|={ao:.3e} "
+          f"|gpu-oracle|/|xi|={agr:.3e} (|xi|/|M| = {wn / np.linalg.norm(Mf):.1f})")
     floor = GRAM_FLOOR if eps < 1e-7 else 0.0
-    assert rel(Yf, Mf) <= 2.0 * eps + floor
-    assert rel(Yf, Rf) <= 3.0 * eps + floor
+    assert ao <= 2.0 * eps
+    assert ag <= 2.0 * eps + floor
+    assert agr <= 3.0 * eps + floor
 
 
 @pytest.mark.parametrize("n,d", [(63, 2), (31, 3), (50, 3)])
