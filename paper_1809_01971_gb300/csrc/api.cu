@@ -121,8 +121,8 @@ size_t layout(fc_ctx* h, Arena& a) {
     w.Tr = a.d(3 * (size_t)CM * CM);
     w.theta = a.d(3 * (size_t)CM);
     w.Vr = a.d(3 * (size_t)CM * CM);
-    w.Z = a.d(3 * (size_t)n * RM);
-    w.Zr = a.d(3 * (size_t)n * RM);
+    w.Z = a.d(3 * nC);
+    w.Zr = a.d(3 * nC);
     w.C = a.d(3 * (size_t)std::max(RM, CM) * K);
     w.wK = a.d((size_t)K);
     w.core = a.d((size_t)RM * RM * RM);
@@ -202,105 +202,118 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     if (K <= 0) { out.rank = 0; return FC_OK; }
     if (K > h->KMAX) return FC_ERANK;
     maxq = std::min(maxq, std::min(out.cap, h->QMAX));
-    const int c = (int)std::min<long long>(K, CM);
+    // Sketch: K <= CM explicit columns (c = cs = K); otherwise CM random columns, of which the
+    // first cs = CM - kHold span the basis and the last kHold estimate the energy it misses.
+    const bool sketch = K > CM;
+    const int c = sketch ? CM : (int)K;
+    const int cs = sketch ? CM - kHold : c;
     const unsigned long long seed = (h->seed += 0x9E3779B97F4A7C15ull);
     int* dims = w.dims;
     CK(cudaMemsetAsync(dims, 0, sizeof(int) * D_SIZE, st));
+    CK(cudaMemsetAsync(w.scal, 0, sizeof(double) * 64, st));
 
-    // ---- stage 1: range of the weighted side matrices W_l --------------------------------
+    // ---- stage 1: range of the weighted side matrices W_l = U_l diag|w| ------------------
     if (kr) {
-        if (K <= CM)
+        if (!sketch)
             launch_kr_cols(st, d, n, kr->Ra, kr->S, kr->E, n, kr->bsE, kr->xa,
                            kr->Yh, n, (long long)n * h->KIN, kr->xb, 1, w.Y, n, nC);
         else
             launch_sketch_kr(st, d, n, kr->Ra, kr->S, c, kr->E, n, kr->bsE, kr->xa,
                              kr->Yh, n, (long long)n * h->KIN, kr->xb, seed, w.Y, n, nC, w.tmp);
     } else {
-        if (K <= CM)
+        if (!sketch)
             launch_scale_cols_abs(st, d, n, (int)K, dn->U, dn->ld, dn->bs, dn->w, w.Y, n, nC);
         else
             launch_sketch_dense(st, d, n, (int)K, c, dn->U, dn->ld, dn->bs, dn->w, seed, w.Y, n, nC);
     }
     CKL();
-    // Orthonormal basis of range(Y) by pivoted Cholesky-QR with one deflation level.
+    // Orthonormal basis of range(Y[:, :cs]) by pivoted Cholesky-QR with one deflation level.
     // A Cholesky factor of the Gram resolves only directions with sigma / sigma_max above
     // ~sqrt(relTol) = 3e-8; the directions it drops are recovered from the remainder
     // Y - Q1 Q1^T Y, which is column-normalised and orthonormalised on its own, then
     // appended to Q1 and re-orthonormalised (span preserved to ~1e-15 relative).
     const long long CC = (long long)CM * CM;
     auto cholqr = [&](const double* src, double* dst, int* rk) {
-        gemm(st, c, c, n, LdT{src, n, nC}, LdN{src, n, nC}, 1.0, 0.0, w.M, CM, CC, d);
-        launch_pchol(st, d, w.M, CM, CC, nullptr, 0, c, 1e-15, w.Tm, CM, CC, rk, 1);
-        gemm(st, n, c, c, LdN{src, n, nC}, LdN{w.Tm, CM, CC}, 1.0, 0.0, dst, n, nC, d);
+        gemm(st, cs, cs, n, LdT{src, n, nC}, LdN{src, n, nC}, 1.0, 0.0, w.M, CM, CC, d);
+        launch_pchol(st, d, w.M, CM, CC, nullptr, 0, cs, 1e-15, w.Tm, CM, CC, rk, 1);
+        gemm(st, n, cs, cs, LdN{src, n, nC}, LdN{w.Tm, CM, CC}, 1.0, 0.0, dst, n, nC, d);
     };
     cholqr(w.Y, w.Q, dims + D_C1);           // Q1 (orthogonal to ~kappa^2 u)
     cholqr(w.Q, w.Y2, dims + D_C1);          // Q1 re-orthonormalised
     // remainder tmp = Y - Q1 (Q1^T Y), columns scaled to unit norm (zero if at rounding level)
-    gemm(st, c, c, n, LdT{w.Y2, n, nC}, LdN{w.Y, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+    gemm(st, cs, cs, n, LdT{w.Y2, n, nC}, LdN{w.Y, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
     CK(cudaMemcpyAsync(w.tmp, w.Y, sizeof(double) * d * nC, cudaMemcpyDeviceToDevice, st));
-    gemm(st, n, c, c, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.tmp, n, nC, d);
-    launch_deflate_normalize(st, d, n, c, w.tmp, n, nC, w.Y, 1e-13);
+    gemm(st, n, cs, cs, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.tmp, n, nC, d);
+    launch_deflate_normalize(st, d, n, cs, w.tmp, n, nC, w.Y, 1e-13);
     cholqr(w.tmp, w.Q, dims + D_CR);         // Q2
     // Q2 <- Q2 - Q1 (Q1^T Q2), re-orthonormalised
-    gemm(st, c, c, n, LdT{w.Y2, n, nC}, LdN{w.Q, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
-    gemm(st, n, c, c, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.Q, n, nC, d);
+    gemm(st, cs, cs, n, LdT{w.Y2, n, nC}, LdN{w.Q, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+    gemm(st, n, cs, cs, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.Q, n, nC, d);
     cholqr(w.Q, w.GQ, dims + D_CR);
     // [Q1 | Q2] and a final pass; live columns of the basis -> dims[D_C1 + l]
-    launch_combine_cols(st, d, n, c, w.Y2, n, nC, w.GQ, dims + D_C1, dims + D_CR, dims + D_CT);
+    launch_combine_cols(st, d, n, cs, w.Y2, n, nC, w.GQ, dims + D_C1, dims + D_CR, dims + D_CT);
     cholqr(w.Y2, w.Q, dims + D_C1);
     double* Qb = w.Q;
     CKL();
-    // Rayleigh-Ritz matrix T = Q^T W W^T Q and energy tr = ||W||_F^2
+    // Energy the basis misses, (1/kHold) ||(I - Q Q^T) Y_hold||_F^2 (an unbiased estimate of
+    // ||(I - Q Q^T) W||_F^2 for sketch columns W omega with E[omega omega^T] = I); computed
+    // from the projected residual itself, so it is resolved down to rounding level.
+    if (sketch) {
+        double* Yh = w.Y + (long long)cs * n;
+        double* Rh = w.tmp + (long long)cs * n;
+        gemm(st, cs, kHold, n, LdT{Qb, n, nC}, LdN{Yh, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+        CK(cudaMemcpy2DAsync(Rh, sizeof(double) * nC, Yh, sizeof(double) * nC,
+                             sizeof(double) * n * kHold, d, cudaMemcpyDeviceToDevice, st));
+        gemm(st, n, kHold, cs, LdN{Qb, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, Rh, n, nC, d);
+        launch_block_energy(st, d, n * kHold, Rh, nC, 1.0 / kHold, w.scal + 24);
+    }
+    // Rayleigh-Ritz matrix T = Q^T W W^T Q: its eigenvectors order the basis (largest
+    // energy first); the energies themselves are taken from the projections below.
     if (kr) {
         // GY = Yh diag(xb^2) Yh^T ;  T = Q^T (GE . GY) Q
         const long long nn = (long long)n * n;
         gemm(st, n, n, kr->S, LdSq{kr->Yh, n, (long long)n * h->KIN, kr->xb},
              LdT{kr->Yh, n, (long long)n * h->KIN}, 1.0, 0.0, w.GY, n, nn, d);
-        gemm(st, n, c, n, LdHad{kr->GE, w.GY, n, nn, nn}, LdN{Qb, n, nC}, 1.0, 0.0, w.GQ, n, nC, d);
-        gemm(st, c, c, n, LdT{Qb, n, nC}, LdN{w.GQ, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
-        launch_trace_kr(st, d, n, kr->GE, n, nn, w.GY, n, nn, w.scal + 0);
+        gemm(st, n, cs, n, LdHad{kr->GE, w.GY, n, nn, nn}, LdN{Qb, n, nC}, 1.0, 0.0, w.GQ, n, nC, d);
+        gemm(st, cs, cs, n, LdT{Qb, n, nC}, LdN{w.GQ, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
         launch_kr_wnorm(st, kr->Ra, kr->xa, kr->S, kr->xb, w.scal + 4);
+        launch_outer_weights(st, kr->Ra, kr->xa, kr->S, kr->xb, w.wK);
     } else {
-        // Bq = Q^T W (c x K) in w.C (ld CM ... reuse C region), T = Bq Bq^T
+        // Bq = Q^T W (cs x K) in w.C, T = Bq Bq^T
         double* Bq = w.C;
-        gemm(st, c, (int)K, n, LdT{Qb, n, nC}, LdAbsN{dn->U, dn->ld, dn->bs, dn->w}, 1.0, 0.0, Bq,
+        gemm(st, cs, (int)K, n, LdT{Qb, n, nC}, LdAbsN{dn->U, dn->ld, dn->bs, dn->w}, 1.0, 0.0, Bq,
              CM, (long long)CM * K, d);
-        gemm(st, c, c, (int)K, LdN{Bq, CM, (long long)CM * K}, LdT{Bq, CM, (long long)CM * K}, 1.0,
+        gemm(st, cs, cs, (int)K, LdN{Bq, CM, (long long)CM * K}, LdT{Bq, CM, (long long)CM * K}, 1.0,
              0.0, w.Tr, CM, CC, d);
-        launch_weighted_energy(st, d, n, (int)K, dn->U, dn->ld, dn->bs, dn->w, w.scal + 0);
         launch_sumsq(st, (int)K, dn->w, w.scal + 4, 1);
     }
     CKL();
-    launch_jacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, c, w.theta, CM, w.Vr, CM, CC);
-    // Tucker ranks: tail <= eps ||w||_2 / sqrt(2d)
-    launch_select_tucker(st, d, w.theta, CM, w.scal + 0, w.scal + 4, eps * eps / (2.0 * d),
-                         std::min(RM, c), dims + D_R, w.scal + 8, dims + D_C1);
-    launch_stage2_dims(st, d, dims);
-    // Z_l = Q_l Vr_l[:, :RM]
-    const int rz = std::min(RM, c);
-    const long long nR = (long long)n * RM;
-    gemm(st, n, rz, c, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nR, d);
-    CKL();
-    // C_l = Z_l^T U_l  (r_l x K), unweighted factors
-    const long long RK = (long long)RM * K;
-    for (int l = 0; l < d; ++l) {
-        if (kr)
-            gemm(st, RM, (int)K, n, LdT{w.Z + l * nR, n, 0},
-                 LdKR{kr->E + l * kr->bsE, n, 0, kr->Yh + (long long)l * n * h->KIN, n, 0, kr->S},
-                 1.0, 0.0, w.C + l * RK, RM, 0, 1, dims + D_R + l);
-        else
-            gemm(st, RM, (int)K, n, LdT{w.Z + l * nR, n, 0}, LdN{dn->U + l * dn->bs, dn->ld, 0}, 1.0,
-                 0.0, w.C + l * RK, RM, 0, 1, dims + D_R + l);
-    }
-    // signed term weights
+    launch_jacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC);
+    // Zc_l = Q_l Vr_l (all cs Ritz directions, descending)
+    gemm(st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
+    // B2_l = Zc_l^T U_l (cs x K, unweighted): its first r_l rows are the projected factors C_l
+    // of the core; rho_i = sum_K w_K^2 B2[i, K]^2 is the energy of W_l along Ritz direction i
+    const long long RK = (long long)CM * K;
     const double* wK = dn ? dn->w : w.wK;
-    if (kr) launch_outer_weights(st, kr->Ra, kr->xa, kr->S, kr->xb, w.wK);
+    if (kr)
+        gemm(st, cs, (int)K, n, LdT{w.Z, n, nC},
+             LdKR{kr->E, n, kr->bsE, kr->Yh, n, (long long)n * h->KIN, kr->S}, 1.0, 0.0, w.C, CM,
+             RK, d);
+    else
+        gemm(st, cs, (int)K, n, LdT{w.Z, n, nC}, LdN{dn->U, dn->ld, dn->bs}, 1.0, 0.0, w.C, CM, RK,
+             d);
+    launch_row_energy(st, d, cs, (int)K, w.C, CM, RK, wK, w.theta, CM);
+    // Tucker ranks: smallest r_l with sum_{i >= r_l} rho_i + missed <= (eps ||w||_2)^2 / (2d)
+    launch_select_tucker(st, d, w.theta, CM, w.scal + 24, w.scal + 4, eps * eps / (2.0 * d),
+                         std::min(RM, cs), dims + D_R, w.scal + 8, dims + D_C1);
+    launch_stage2_dims(st, d, dims);
+    const int rz = std::min(RM, cs);
     CKL();
     // ---- core: B3[(a + r0 b), c] = sum_K w_K C0[a,K] C1[b,K] C2[c,K] ----------------------
     const int RR = RM * RM;
-    LdCore A{w.C, w.C + RK, wK, RM, dims + D_R};
+    LdCore A{w.C, w.C + RK, wK, CM, dims + D_R};
     if (d == 3)
-        gemm(st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, RM, 0}, 1.0, 0.0, w.core, RR, 0, 1,
+        gemm(st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, CM, 0}, 1.0, 0.0, w.core, RR, 0, 1,
              dims + D_R12, dims + D_R3, nullptr);
     else
         gemm(st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, w.core, RR, 0, 1, dims + D_R12, nullptr,
@@ -317,6 +330,8 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     gemm(st, RM, RM, RM, LdSlT{w.Srot, RR, dims + D_R}, LdSl{w.Srot, RR, dims + D_R}, 1.0, 0.0,
          w.SG, RM, RR, (d == 3) ? RM : 1, dims + D_R + 1, dims + D_R + 1, dims + D_R);
     launch_jacobi(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR);
+    // candidate term energies ||S_s y_i||^2 taken directly (not the Gram eigenvalues)
+    launch_slice_energy(st, (d == 3) ? RM : 1, RM, dims, w.Srot, RR, w.Vs, RM, RR, w.mus, RM);
     CKL();
     launch_select_terms(st, w.mus, RM, dims + D_R3, dims + D_NPER, RM, RM, w.scal + 12,
                         eps * eps / 2.0, maxq, dims + D_Q, w.sigma, w.tslice, w.tidx, w.scal + 16);
@@ -327,13 +342,13 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     // ---- output factors U'_l = Z_l X_l (eigen-index domain: F (Z_l X_l)) ------------------
     const double* Zuse = w.Z;
     if (kr) {
-        const double* in[3] = {w.Z, w.Z + nR, w.Z + 2 * nR};
-        double* o[3] = {w.Zr, w.Zr + nR, w.Zr + 2 * nR};
+        const double* in[3] = {w.Z, w.Z + nC, w.Z + 2 * nC};
+        double* o[3] = {w.Zr, w.Zr + nC, w.Zr + 2 * nC};
         dst_cols(h, st, rz, in, n, o, n);
         Zuse = w.Zr;
     }
     for (int l = 0; l < d; ++l)
-        gemm(st, n, maxq, RM, LdN{Zuse + l * nR, n, 0}, LdN{w.X + l * RQ, RM, 0}, 1.0, 0.0,
+        gemm(st, n, maxq, RM, LdN{Zuse + l * nC, n, 0}, LdN{w.X + l * RQ, RM, 0}, 1.0, 0.0,
              out.U[l], out.ld, 0, 1, nullptr, dims + D_Q, dims + D_R + l);
     CK(cudaMemcpyAsync(out.xi, w.sigma, sizeof(double) * maxq, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->hint, dims, sizeof(int) * D_SIZE, cudaMemcpyDeviceToHost, st));

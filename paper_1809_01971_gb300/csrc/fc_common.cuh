@@ -196,9 +196,9 @@ inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha,
     if (M <= 0 || N <= 0 || batch <= 0) return;
     const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
     int splits = 1;
-    if (tiles < 2 * kNumSMs && K >= 256) {
-        long long want = (2 * kNumSMs + tiles - 1) / tiles;
-        long long most = (K + 127) / 128;          // at least 128 of K per split
+    if (tiles < 2 * kNumSMs && K >= 128) {
+        long long want = (4 * kNumSMs + tiles - 1) / tiles;
+        long long most = (K + 63) / 64;            // at least 64 of K per split
         splits = (int)std::min<long long>(std::min(want, most), 64);
     }
     int kchunk = K;

@@ -13,9 +13,11 @@ void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long lo
 void launch_pchol(cudaStream_t st, int batch, const double* M, int ldm, long long bsM,
                   const int* dims, int dstride, int cmax, double relTol, double* T, int ldt,
                   long long bsT, int* rank, int rstride);
-void launch_select_tucker(cudaStream_t st, int d, const double* theta, int ldth, const double* tr,
-                          const double* wn2, double epsfac2, int cap, int* r_out,
-                          double* tail2_out, int* live);
+// Tucker rank per mode: smallest r with sum_{i >= r} rho[i] + missed <= epsfac2 * wn2
+// (rho: energies along the ordered basis directions, live entries dims live[l]).
+void launch_select_tucker(cudaStream_t st, int d, const double* rho, int ldrho,
+                          const double* missed, const double* wn2, double epsfac2, int cap,
+                          int* r_out, double* tail2_out, const int* live);
 void launch_select_terms(cudaStream_t st, const double* mu, int ldmu, const int* nslice,
                          const int* nper, int smax, int pmax, const double* core_e, double frac2,
                          int maxq, int* q_out, double* sigma, int* tslice, int* tidx,
@@ -58,6 +60,16 @@ void launch_combine_cols(cudaStream_t st, int d, int n, int c, double* Q, int ld
 void launch_trace_kr(cudaStream_t st, int d, int n, const double* GE, int lde, long long bsE,
                      const double* GY, int ldy, long long bsY, double* tr);
 void launch_sumsq(cudaStream_t st, int K, const double* w, double* out, int nout);
+// out[l] = scale * sum_{e < count} p[l*stride + e]^2
+void launch_block_energy(cudaStream_t st, int d, long long count, const double* p,
+                         long long stride, double scale, double* out);
+// rho[l*ldrho + i] = sum_{k < K} w_k^2 B[l*bs + i + k*ld]^2, i < rows
+void launch_row_energy(cudaStream_t st, int d, int rows, int K, const double* B, int ld,
+                       long long bs, const double* w, double* rho, int ldrho);
+// mus[s*ldmu + i] = ||S_s y_{s,i}||^2 for slices s < dims[D_R3], i < dims[D_R+1]
+void launch_slice_energy(cudaStream_t st, int smax, int rmax, const int* dims, const double* S,
+                         long long ldS, const double* V, int ldv, long long bsV, double* mus,
+                         int ldmu);
 // ||w_a||^2 * ||w_b||^2 (KR weight norm); out[0]
 void launch_kr_wnorm(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,
                      double* out);
@@ -89,12 +101,14 @@ void launch_stage2_dims(cudaStream_t st, int d, int* dims);
 }  // namespace fc
 
 namespace fc {
+// Held-out sketch columns that estimate the energy outside the sketched basis.
+constexpr int kHold = 8;
 // Layout of the per-truncation device dims array (ints).
 enum {
     D_R = 0,        // [0..2] Tucker ranks r_l after stage 1
     D_R12 = 3,      // r_0 * r_1 (rows of the core unfolding)
     D_R3 = 4,       // r_2 (d = 3) or 1 (d = 2)
-    D_NPER = 5,     // min(r_0, r_1): canonical terms per slice
+    D_NPER = 5,     // r_1: candidate canonical terms per slice
     D_Q = 6,        // selected canonical rank
     D_C1 = 8,       // [8..10]  sketch rank after pass 1 (per mode)
     D_CR = 11,      // [11..13] rank of the deflated remainder

@@ -273,36 +273,36 @@ void launch_pchol(cudaStream_t st, int batch, const double* M, int ldm, long lon
 }
 
 // ---------------------------------------------------------------------------------------
-// Tucker-rank choice (stage 1): theta (descending Ritz values of the weighted side-matrix
-// Gram) of mode l, total energy tr = ||W_l||_F^2.  r = smallest r >= 1 with
-// tr - sum_{i<r} theta_i <= thr^2, clamped to [1, min(cap, live)].  Writes r and the
-// squared tail into out arrays.
+// Tucker-rank choice (stage 1).  rho[i] (i < live) is the energy of the weighted side matrix
+// W_l along basis direction i (directions ordered by decreasing Ritz value), computed from
+// the projection itself; missed[l] the energy outside the basis.  Projecting onto the first
+// r directions loses exactly tail(r) = sum_{i >= r} rho[i] + missed, so r = the smallest
+// r >= 1 with tail(r) <= thr^2, clamped to min(cap, live).
 // ---------------------------------------------------------------------------------------
-__global__ void select_tucker_kernel(int d, const double* theta, int ldth, const double* tr,
+__global__ void select_tucker_kernel(int d, const double* rho, int ldrho, const double* missed,
                                      const double* wn2, double epsfac2, int cap, int* r_out,
-                                     double* tail2_out, int* live)
+                                     double* tail2_out, const int* live)
 {
     int l = threadIdx.x;
     if (l >= d) return;
     const double thr2 = epsfac2 * (*wn2);
-    const double* th = theta + (long long)l * ldth;
-    int lim = cap;
-    if (live) lim = min(lim, live[l]);
-    double t = tr[l];
-    int r = 0;
-    double tail = t;
-    while (r < lim && tail > thr2) { tail -= fmax(th[r], 0.0); ++r; }
-    if (r < 1) { r = 1; tail = t - fmax(th[0], 0.0); }
+    const double* rh = rho + (long long)l * ldrho;
+    const int nl = live[l];
+    const int lim = max(1, min(cap, nl));
+    double tail = fmax(missed[l], 0.0);
+    for (int i = nl - 1; i >= lim; --i) tail += fmax(rh[i], 0.0);   // always dropped
+    int r = lim;
+    while (r > 1 && tail + fmax(rh[r - 1], 0.0) <= thr2) { tail += fmax(rh[r - 1], 0.0); --r; }
     r_out[l] = r;
-    tail2_out[l] = fmax(tail, 0.0);
+    tail2_out[l] = tail;
 }
 
-void launch_select_tucker(cudaStream_t st, int d, const double* theta, int ldth, const double* tr,
-                          const double* wn2, double epsfac2, int cap, int* r_out,
-                          double* tail2_out, int* live)
+void launch_select_tucker(cudaStream_t st, int d, const double* rho, int ldrho,
+                          const double* missed, const double* wn2, double epsfac2, int cap,
+                          int* r_out, double* tail2_out, const int* live)
 {
-    note_launch(); select_tucker_kernel<<<1, 32, 0, st>>>(d, theta, ldth, tr, wn2, epsfac2, cap, r_out, tail2_out,
-                                           live);
+    note_launch(); select_tucker_kernel<<<1, 32, 0, st>>>(d, rho, ldrho, missed, wn2, epsfac2, cap, r_out,
+                                                          tail2_out, live);
 }
 
 // ---------------------------------------------------------------------------------------

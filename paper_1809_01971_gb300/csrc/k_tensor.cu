@@ -308,6 +308,81 @@ void launch_sumsq(cudaStream_t st, int K, const double* w, double* out, int nout
     note_launch(); sumsq_kernel<<<1, 256, 0, st>>>(K, w, out, nout);
 }
 
+__global__ void block_energy_kernel(long long count, const double* p, long long stride,
+                                    double scale, double* out)
+{
+    __shared__ double red[32];
+    const int l = blockIdx.x;
+    double s = 0.0;
+    for (long long e = threadIdx.x; e < count; e += blockDim.x) {
+        double v = p[l * stride + e];
+        s += v * v;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[l] = scale * s;
+}
+
+void launch_block_energy(cudaStream_t st, int d, long long count, const double* p,
+                         long long stride, double scale, double* out)
+{
+    note_launch(); block_energy_kernel<<<d, 512, 0, st>>>(count, p, stride, scale, out);
+}
+
+// one CTA per (row i, mode l): sum over the K columns of a row of a column-major matrix
+__global__ void row_energy_kernel(int K, const double* B, int ld, long long bs, const double* w,
+                                  double* rho, int ldrho)
+{
+    __shared__ double red[32];
+    const int i = blockIdx.x, l = blockIdx.y;
+    const double* row = B + l * bs + i;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double v = w[k] * row[(long long)k * ld];
+        s += v * v;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) rho[(long long)l * ldrho + i] = s;
+}
+
+void launch_row_energy(cudaStream_t st, int d, int rows, int K, const double* B, int ld,
+                       long long bs, const double* w, double* rho, int ldrho)
+{
+    if (rows <= 0) return;
+    note_launch(); row_energy_kernel<<<dim3(rows, d), 256, 0, st>>>(K, B, ld, bs, w, rho, ldrho);
+}
+
+// mus[s*ldmu + i] = ||S_s y_i||^2, S_s compact r0 x r1 at S + s*ldS (element (a,b) at a + r0 b),
+// y_i = column i of V + s*bsV (ld ldv).  One CTA per slice, one warp per candidate i.
+__global__ void slice_energy_kernel(int rmax, const int* dims, const double* S, long long ldS,
+                                    const double* V, int ldv, long long bsV, double* mus, int ldmu)
+{
+    const int s = blockIdx.x;
+    if (s >= dims[D_R3]) return;
+    const int r0 = dims[D_R + 0], r1 = dims[D_R + 1];
+    const double* Ss = S + s * ldS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < r1; i += nw) {
+        const double* y = V + s * bsV + (long long)i * ldv;
+        double e = 0.0;
+        for (int a = lane; a < r0; a += 32) {
+            double v = 0.0;
+            for (int b = 0; b < r1; ++b) v += Ss[a + r0 * b] * y[b];
+            e += v * v;
+        }
+        e = warp_sum(e);
+        if (lane == 0) mus[(long long)s * ldmu + i] = e;
+    }
+    (void)rmax;
+}
+
+void launch_slice_energy(cudaStream_t st, int smax, int rmax, const int* dims, const double* S,
+                         long long ldS, const double* V, int ldv, long long bsV, double* mus,
+                         int ldmu)
+{
+    if (smax <= 0) return;
+    note_launch(); slice_energy_kernel<<<smax, 256, 0, st>>>(rmax, dims, S, ldS, V, ldv, bsV, mus, ldmu);
+}
+
 __global__ void kr_wnorm_kernel(int Ra, const double* xa, int S, const double* xb, double* out)
 {
     __shared__ double red[32];
@@ -516,7 +591,7 @@ __global__ void stage2_dims_kernel(int d, int* dims)
     int r0 = dims[D_R + 0], r1 = dims[D_R + 1];
     dims[D_R12] = r0 * r1;
     dims[D_R3] = (d == 3) ? dims[D_R + 2] : 1;
-    dims[D_NPER] = min(r0, r1);
+    dims[D_NPER] = r1;
 }
 
 void launch_stage2_dims(cudaStream_t st, int d, int* dims)

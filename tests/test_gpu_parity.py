@@ -284,11 +284,11 @@ def test_solve_config1_2d(fc):
     assert e < 1e-7
 
 
-@pytest.mark.parametrize("problem", [0, 3, 5])
+@pytest.mark.parametrize("problem", [0, 3, 4, 5])
 def test_solve_config2_3d_n255(fc, problem):
-    """3D, n=255, 4 Gaussians + sine mode: CP-PCG vs the full oracle (16.6M points).
-    The solutions need ~50-100 canonical terms at 1e-6..1e-7, so the cap is 96."""
+    """3D, n=255, 4 Gaussians + sine mode: CP-PCG vs the full oracle (16.6M points), at the
+    workload's settings (eps = 1e-9, tol = 1e-8, cap 192): error <= 1e-6."""
     prob = fi.config2(problem)
-    info, e = _solve_vs_full(fc, prob, 1e-7, 1e-7, max_rank=96)
+    info, e = _solve_vs_full(fc, prob, prob.tol, prob.eps, max_rank=prob.max_rank)
     assert info.status == 0
     assert e < 1e-6
