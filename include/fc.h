@@ -171,6 +171,21 @@ int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream);
 int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev_tmp,
                   void* stream);
 
+/* <x, y> like fc_inner, without a handle and without allocating: for callers that cannot call
+ * cudaMalloc (inside a graph capture that must not allocate, hosts that hand out device memory
+ * themselves, loops that forbid allocation after start-up).  The paper has no counterpart.
+ *  - x, y: CP tensors as in fc_inner (same d and n, d in {2,3}); dev_out: DEVICE pointer that
+ *    receives the one double.  Stream-ordered on `stream`; nothing is synchronised.
+ *  - Scratch is a file-scope device array of 3 * FC_STATIC_MAX_RANK^2 doubles (384 KiB) that
+ *    every GPU which loads the library holds until the process exits; ranks above
+ *    FC_STATIC_MAX_RANK return FC_ERANK.  No cudaMalloc, cudaFree or allocating library call.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - All calls share the one array: calls whose work overlaps on the GPU (other streams or
+ *    threads) race and must be serialised by the caller. */
+#define FC_STATIC_MAX_RANK 128
+int fc_inner_static(const fc_cp* x, const fc_cp* y, double* dev_out, void* stream);
+
 void fc_destroy(fc_handle h);
 const char* fc_strerror(int code);
 const char* fc_last_cuda_error(void);

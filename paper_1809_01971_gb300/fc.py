@@ -100,6 +100,7 @@ def lib() -> C.CDLL:
             "fc_strerror": (C.c_char_p, [I]),
             "fc_last_cuda_error": (C.c_char_p, []),
             "fc_launch_count": (C.c_ulonglong, []),
+            "fc_inner_static": (I, [cp_p, cp_p, V, V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -286,6 +287,15 @@ def fc_to_full(h: Handle, x: CP, out: Optional[torch.Tensor] = None, stream=None
                                           _stream(stream)))
     # column-major with i_1 fastest -> numpy axis order reversed
     return out.view(*([n] * d)).permute(*reversed(range(d)))
+
+
+def fc_inner_static(x: CP, y: CP, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """<x, y> into the device scalar ``out`` without a handle or any allocation."""
+    if out.dtype != torch.float64 or not out.is_cuda:
+        raise ValueError("out must be a CUDA float64 tensor")
+    _check("fc_inner_static", lib().fc_inner_static(C.byref(x.desc()), C.byref(y.desc()),
+                                                    C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
 
 
 def fc_launch_count() -> int:
