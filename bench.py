@@ -168,6 +168,13 @@ def run_reference(args):
     return 0
 
 
+# FP64 peak of the chip from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
+# x 2 flop x 2.07 GHz (an FP64 probe on this part measured 1.19 TFLOP/s at 1.9-2.07 GHz).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# Jacobi kernel DRAM traffic per launch from ncu (None until captured for this build).
+JACOBI_TRAFFIC_BYTES = None
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -185,7 +192,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
+    main_stream = torch.cuda.current_stream()
     probs = problems(args.problems)
     # independent problems: each rank solves the full six-problem set (weak scaling)
     hs, Bs, Us = [], [], []
@@ -194,13 +201,34 @@ def main():
         hs.append(h)
         Bs.append(fc.CP.from_factors(*p.rhs(), device=dev))
         Us.append(fc.CP(p.d, p.n, p.max_rank, device=dev))
+    streams = [torch.cuda.Stream(device=dev) for _ in probs]
+    tols = [p.tol for p in probs]
+    epss = [p.eps for p in probs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
-        infos = []
-        for p, h, B, U in zip(probs, hs, Bs, Us):
-            infos.append(fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=stream))
-        return infos
+        # the step's problems run concurrently, one stream each (fc_solve_batched)
+        return fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss)
+
+    def step_sequential():
+        return [fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=main_stream)
+                for p, h, B, U in zip(probs, hs, Bs, Us)]
+
+    def timed(fn):
+        """Device time of fn() from CUDA events: start on the main stream, every problem
+        stream waits on it, and the main stream waits for every problem stream at the end."""
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main_stream)
+        for s_ in streams:
+            s_.wait_event(e0)
+        out = fn()
+        for s_ in streams:
+            main_stream.wait_stream(s_)
+        e1.record(main_stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
 
     for _ in range(args.warmup):
         step()
@@ -213,22 +241,17 @@ def main():
 
     sampler = ClockSampler(local)
     sampler.start()
-    times = []
+    times, iters = [], []
+    barrier()
+    fc.fc_prof_enable(fc.fc.PROF_JACOBI)
     launches0 = fc.fc_launch_count()
-    iters = []
-    barrier()
     for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        infos = step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        ms, infos = timed(step)
+        times.append(ms)
         iters.append([i.iters for i in infos])
-    barrier()
     launches = fc.fc_launch_count() - launches0
+    jac_n, jac_ms, jac_work = fc.fc_prof_read()
+    barrier()
     clocks = sampler.stop()
     t_total = sum(times) / 1e3
     if world > 1:
@@ -237,6 +260,11 @@ def main():
         t_total = float(t.item())
     solves = len(probs) * args.steps * world
     value = solves / t_total
+
+    # the same problems one after another on one stream (context for the batched number)
+    seq_steps = max(1, args.steps // 2)
+    seq_ms = sum(timed(step_sequential)[0] for _ in range(seq_steps))
+    seq_value = len(probs) * seq_steps / (seq_ms / 1e3)
 
     # end to end through the public API with host buffers
     host_in = []
@@ -250,28 +278,23 @@ def main():
     d2h = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_out)
 
     def e2e_step():
-        for (xi_h, U_h), (xo, Uo), p, h, B, U in zip(host_in, host_out, probs, hs, Bs, Us):
+        for (xi_h, U_h), p, B, s_ in zip(host_in, probs, Bs, streams):
             R = xi_h.numel()
-            B.xi[:R].copy_(xi_h, non_blocking=True)
-            B.U[:, :R, :p.n].copy_(U_h, non_blocking=True)
+            with torch.cuda.stream(s_):
+                B.xi[:R].copy_(xi_h, non_blocking=True)
+                B.U[:, :R, :p.n].copy_(U_h, non_blocking=True)
             B.rank = R
-            fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=stream)
-            xo.copy_(U.xi[:p.max_rank], non_blocking=True)
-            Uo.copy_(U.U[:, :p.max_rank, :p.n], non_blocking=True)
-        stream.synchronize()
+        fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss)
+        for (xo, Uo), p, U, s_ in zip(host_out, probs, Us, streams):
+            with torch.cuda.stream(s_):
+                xo.copy_(U.xi[:p.max_rank], non_blocking=True)
+                Uo.copy_(U.U[:, :p.max_rank, :p.n], non_blocking=True)
 
-    e2e_step()
+    timed(e2e_step)
     e2e_times = []
     barrier()
     for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e2e_step()
-        e1.record(stream)
-        e1.synchronize()
-        e2e_times.append(e0.elapsed_time(e1))
+        e2e_times.append(timed(e2e_step)[0])
     barrier()
     e2e_t = sum(e2e_times) / 1e3
     if world > 1:
@@ -292,6 +315,17 @@ def main():
         fc.fc_to_full(h, U, out=tmp)
         err = float(torch.linalg.norm(tmp - full_u) / torch.linalg.norm(full_u))
         max_err = max(max_err, err)
+    roofline = None
+    if jac_n > 0 and jac_ms > 0:
+        achieved = jac_work / jac_n / (jac_ms / jac_n * 1e-3) / 1e12     # TFLOP/s
+        peak = FP64_PEAK_GFLOPS / 1e3
+        roofline = {"kernel": "jacobi_eig_kernel (FP64 symmetric eigen-solves of the RHOSVD)",
+                    "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": JACOBI_TRAFFIC_BYTES,
+                    "peak_kind": "FP64, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                    "work": "9 c^3 flop per c x c matrix (textbook dense eigen-solve count)",
+                    "launches": jac_n, "avg_launch_us": 1e3 * jac_ms / jac_n,
+                    "share_of_step_time": jac_ms / (t_total * 1e3) / (1 if world == 1 else world)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -300,13 +334,15 @@ def main():
                 "config": {"workload": WORKLOAD, "problems_per_step": len(probs),
                            "l2": "flushed between steps (512 MiB write, untimed)",
                            "setup": "per operator, before timing",
+                           "concurrency": "fc_solve_batched: one stream and host thread per problem",
                            "pcg_iters": iters[-1]},
+                "sequential_value": seq_value,
                 "max_rel_err_vs_full": max_err,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches),
                 "clocks": clocks,
-                "roofline": None,
+                "roofline": roofline,
                 "cpu_baseline": None}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(probs)

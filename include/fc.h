@@ -161,6 +161,16 @@ int fc_inner(fc_handle h, const fc_cp* x, const fc_cp* y, double* out_host, void
 int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* opts,
              fc_solve_info* info, void* stream);
 
+/* `count` independent solves (each as fc_solve on its own handle, right-hand side rhs[i],
+ * solution u[i], options opts[i] (opts may be NULL), info[i]), run concurrently: one host
+ * thread per problem drives Algorithm 1 on streams[i].  A single solve keeps only a few of
+ * the 152 SMs busy (its small FP64 eigen-solves run on one CTA each), so independent problems
+ * overlap on the device.  Handles and streams must be pairwise distinct (FC_EINVAL otherwise);
+ * the calling thread's current device is used.  Returns FC_OK if every solve returned FC_OK,
+ * else the first failing problem's code; info[i].status holds each problem's own status. */
+int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
+                     const fc_solve_opts* opts, fc_solve_info* info, void* const* streams);
+
 /* Expand a CP tensor to the full n^d array, column-major (i_1 fastest). */
 int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream);
 
@@ -193,6 +203,15 @@ const char* fc_last_cuda_error(void);
 /* Number of CUDA kernels libfc has launched in this process so far (all handles, all
  * devices); a host-side counter for instrumentation, no synchronisation. */
 unsigned long long fc_launch_count(void);
+
+/* Kernel-class instrumentation.  fc_prof_enable(kclass) synchronises the device, clears the
+ * counters and, until fc_prof_read, brackets every launch of that class with a pair of CUDA
+ * events on its stream and accumulates the class's algorithmic work on the device.
+ * kclass: 0 = off, 1 = the FP64 Jacobi eigensolver (work = 9 c^3 flops per c x c matrix).
+ * fc_prof_read disables it, synchronises, and returns the launches, the summed event time of
+ * those launches in ms, and the work (flops). */
+int fc_prof_enable(int kclass);
+int fc_prof_read(long long* launches, double* total_ms, double* work);
 
 #ifdef __cplusplus
 }

@@ -11,8 +11,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace fc;
@@ -22,6 +24,32 @@ using namespace fc;
 namespace fc {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Instrumentation state: one enabled kernel class, a growing pool of event pairs.
+static std::mutex g_prof_mu;
+static std::atomic<int> g_prof_class{KC_NONE};
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
+static size_t g_prof_used = 0;
+
+bool prof_active(int kclass) { return g_prof_class.load(std::memory_order_relaxed) == kclass; }
+
+void prof_begin(cudaStream_t st, ProfMark& m) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    if (g_prof_used == g_prof_events.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+        g_prof_events.emplace_back(a, b);
+    }
+    m.slot = (int)g_prof_used++;
+    cudaEventRecord(g_prof_events[m.slot].first, st);
+}
+
+void prof_end(cudaStream_t st, const ProfMark& m) {
+    if (m.slot < 0) return;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    cudaEventRecord(g_prof_events[m.slot].second, st);
+}
 }  // namespace fc
 
 namespace {
@@ -436,6 +464,40 @@ const char* fc_strerror(int code) {
 
 const char* fc_last_cuda_error(void) { return g_cuda_msg.c_str(); }
 
+int fc_prof_enable(int kclass) {
+    if (kclass < 0 || kclass > KC_JACOBI) return FC_EINVAL;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError());
+    g_prof_used = 0;
+    unsigned long long* w = prof_work_counter();
+    if (!w) return FC_ECUDA;
+    CK(cudaMemset(w, 0, sizeof(unsigned long long)));
+    CK(cudaDeviceSynchronize());
+    g_prof_class.store(kclass);
+    return FC_OK;
+}
+
+int fc_prof_read(long long* launches, double* total_ms, double* work) {
+    if (!launches || !total_ms || !work) return FC_EINVAL;
+    g_prof_class.store(KC_NONE);
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    CK(cudaDeviceSynchronize());
+    double tot = 0.0;
+    for (size_t i = 0; i < g_prof_used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g_prof_events[i].first, g_prof_events[i].second));
+        tot += ms;
+    }
+    unsigned long long wk = 0;
+    unsigned long long* w = prof_work_counter();
+    if (!w) return FC_ECUDA;
+    CK(cudaMemcpy(&wk, w, sizeof(wk), cudaMemcpyDeviceToHost));
+    *launches = (long long)g_prof_used;
+    *total_ms = tot;
+    *work = (double)wk;
+    return FC_OK;
+}
+
 unsigned long long fc_launch_count(void) { return fc::g_launches.load(std::memory_order_relaxed); }
 
 int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
@@ -457,6 +519,19 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     opts.max_tucker = std::min(opts.max_tucker, kMaxC - 8);
     opts.max_rank = std::min(opts.max_rank, opts.max_tucker * opts.max_tucker);
     if (opts.max_input_rank <= 0) opts.max_input_rank = opts.max_rank;
+    {
+        // kernel attributes are per device: set them once for every device a handle uses
+        static std::mutex mu;
+        static bool done[64] = {false};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FC_ECUDA;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done[dev]) {
+            cudaError_t e = set_linalg_attributes();
+            if (e != cudaSuccess) return cuda_fail(e);
+            done[dev] = true;
+        }
+    }
     SymbolNodes sym, pc;
     if (!build_control_nodes(n, d, alpha, beta, gamma, opts.delta_sym, sym)) return FC_ESETUP;
     if (!build_precond_nodes(n, d, alpha, beta, gamma, opts.precond_rank, pc)) return FC_ESETUP;
@@ -759,6 +834,33 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         rz = rzn;
     }
     return finish(FC_ENOCONV);
+}
+
+int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
+                     const fc_solve_opts* opts, fc_solve_info* info, void* const* streams) {
+    if (count < 0 || (count > 0 && (!h || !rhs || !u || !info || !streams))) return FC_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!h[i]) return FC_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (h[j] == h[i] || streams[j] == streams[i]) return FC_EINVAL;   // no shared state
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FC_ECUDA;
+    std::vector<int> rc(count, FC_OK);
+    std::vector<std::thread> workers;
+    workers.reserve(count);
+    for (int i = 0; i < count; ++i)
+        workers.emplace_back([&, i]() {
+            if (cudaSetDevice(dev) != cudaSuccess) { rc[i] = FC_ECUDA; return; }
+            rc[i] = fc_solve(h[i], &rhs[i], &u[i], opts ? &opts[i] : nullptr, &info[i], streams[i]);
+            if (rc[i] != FC_OK && (rc[i] == FC_EINVAL || rc[i] == FC_ERANK ||
+                                   rc[i] == FC_EWORKSPACE || rc[i] == FC_ECUDA))
+                info[i].status = rc[i];
+        });
+    for (auto& t : workers) t.join();
+    for (int i = 0; i < count; ++i)
+        if (rc[i] != FC_OK) return rc[i];
+    return FC_OK;
 }
 
 int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream) {

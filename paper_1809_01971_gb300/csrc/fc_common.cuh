@@ -12,6 +12,15 @@ namespace fc {
 // Count of kernels launched by this library in this process (fc_launch_count).
 void note_launch();
 
+// Kernel-class timing for instrumentation (fc_prof_*): while a class is enabled, each of
+// its launches is bracketed by a pair of CUDA events recorded on the launching stream.
+enum KernelClass { KC_NONE = 0, KC_JACOBI = 1 };
+struct ProfMark { int slot = -1; };
+bool prof_active(int kclass);
+void prof_begin(cudaStream_t st, ProfMark& m);
+void prof_end(cudaStream_t st, const ProfMark& m);
+unsigned long long* prof_work_counter();   // device counter of the class's algorithmic flops
+
 constexpr int kMaxC = 64;       // largest dense eigen / Cholesky problem handled by one CTA
 constexpr int kThreads = 256;
 

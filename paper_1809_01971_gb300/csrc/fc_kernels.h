@@ -7,6 +7,9 @@ namespace fc {
 
 // ---- k_linalg.cu ---------------------------------------------------------------------
 size_t jacobi_smem(int cmax);
+size_t pchol_smem();
+// Opt the large-shared-memory kernels in to their dynamic shared memory (per device).
+cudaError_t set_linalg_attributes();
 void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
                    const int* dims, int dstride, int cmax, double* ev, long long bsE,
                    double* V, int ldv, long long bsV);

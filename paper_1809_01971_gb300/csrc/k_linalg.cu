@@ -9,6 +9,11 @@
 
 namespace fc {
 
+// Algorithmic work counter of the instrumented kernel class (see prof_* in api.cu):
+// a symmetric eigen-decomposition with eigenvectors counts 9 c^3 flops (Householder
+// tridiagonalisation + implicit QR with accumulation, the textbook figure).
+__device__ unsigned long long g_prof_work = 0;
+
 // ---------------------------------------------------------------------------------------
 // Jacobi eigen-decomposition.  Item b: symmetric c x c matrix at A + b*bsA (ld lda),
 // c = dims ? min(dims[b*dstride], cmax) : cmax.  Writes eigenvalues in descending order to
@@ -20,13 +25,15 @@ __global__ void __launch_bounds__(256)
 jacobi_eig_kernel(const double* __restrict__ A, int lda, long long bsA,
                   const int* __restrict__ dims, int dstride, int cmax,
                   double* __restrict__ ev, long long bsE,
-                  double* __restrict__ V, int ldv, long long bsV, int maxSweeps)
+                  double* __restrict__ V, int ldv, long long bsV, int maxSweeps, int prof)
 {
     extern __shared__ double sm[];
     const int b = blockIdx.x;
     int c = cmax;
     if (dims) c = min(dims[b * dstride], cmax);
     if (c < 0) c = 0;
+    if (prof && threadIdx.x == 0)
+        atomicAdd(&g_prof_work, 9ull * (unsigned long long)c * c * c);
     const int m = (c + 1) & ~1;           // even number of players
     const int S = m + 1;                  // smem row stride
     double* a = sm;                       // m x S
@@ -157,14 +164,19 @@ void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long lo
 {
     if (batch <= 0) return;
     size_t sm = jacobi_smem(cmax);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)jacobi_smem(kMaxC));
-        attr = true;
-    }
+    const bool prof = prof_active(KC_JACOBI);
+    ProfMark mark;
+    if (prof) prof_begin(st, mark);
     note_launch(); jacobi_eig_kernel<<<batch, 256, sm, st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv,
-                                               bsV, 30);
+                                               bsV, 30, prof ? 1 : 0);
+    if (prof) prof_end(st, mark);
+}
+
+unsigned long long* prof_work_counter()
+{
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_prof_work) != cudaSuccess) return nullptr;
+    return static_cast<unsigned long long*>(p);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -257,17 +269,24 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
     if (threadIdx.x == 0) rank[b * rstride] = r;
 }
 
+size_t pchol_smem() { return sizeof(double) * 3 * kMaxC * (kMaxC + 1); }
+
+cudaError_t set_linalg_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)jacobi_smem(kMaxC));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pchol_smem());
+}
+
 void launch_pchol(cudaStream_t st, int batch, const double* M, int ldm, long long bsM,
                   const int* dims, int dstride, int cmax, double relTol, double* T, int ldt,
                   long long bsT, int* rank, int rstride)
 {
     if (batch <= 0) return;
-    const size_t sm = sizeof(double) * 3 * kMaxC * (kMaxC + 1);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-    }
+    const size_t sm = pchol_smem();
     note_launch(); pchol_kernel<<<batch, 256, sm, st>>>(M, ldm, bsM, dims, dstride, cmax, relTol, T, ldt, bsT,
                                          rank, rstride);
 }

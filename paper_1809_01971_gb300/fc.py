@@ -94,6 +94,8 @@ def lib() -> C.CDLL:
             "fc_inner": (I, [P, cp_p, cp_p, C.POINTER(D), V]),
             "fc_apply_trunc": (I, [P, I, cp_p, D, I, cp_p, V]),
             "fc_solve": (I, [P, cp_p, cp_p, C.POINTER(fc_solve_opts), C.POINTER(fc_solve_info), V]),
+            "fc_solve_batched": (I, [I, C.POINTER(P), cp_p, cp_p, C.POINTER(fc_solve_opts),
+                                     C.POINTER(fc_solve_info), C.POINTER(V)]),
             "fc_to_full": (I, [P, cp_p, V, V]),
             "fc_full_solve": (I, [P, V, V, V, V]),
             "fc_destroy": (None, [P]),
@@ -101,6 +103,8 @@ def lib() -> C.CDLL:
             "fc_last_cuda_error": (C.c_char_p, []),
             "fc_launch_count": (C.c_ulonglong, []),
             "fc_inner_static": (I, [cp_p, cp_p, V, V]),
+            "fc_prof_enable": (I, [I]),
+            "fc_prof_read": (I, [C.POINTER(C.c_longlong), C.POINTER(D), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -278,6 +282,31 @@ def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
     return info
 
 
+def fc_solve_batched(handles, rhs, us, streams, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
+                     raise_on_fail: bool = True):
+    """Independent solves run concurrently (one host thread and one stream per problem).
+    tol / eps / kmax / max_rank are scalars or per-problem sequences."""
+    count = len(handles)
+
+    def per(v):
+        return list(v) if isinstance(v, (list, tuple)) else [v] * count
+
+    tols, epss, kms, mrs = per(tol), per(eps), per(kmax), per(max_rank)
+    H = (C.c_void_p * count)(*[h.ptr.value for h in handles])
+    R = (fc_cp * count)(*[x.desc() for x in rhs])
+    Uc = (fc_cp * count)(*[x.desc() for x in us])
+    O = (fc_solve_opts * count)(*[fc_solve_opts(float(tols[i]), float(epss[i]), int(kms[i]),
+                                                int(mrs[i])) for i in range(count)])
+    infos = (fc_solve_info * count)()
+    S = (C.c_void_p * count)(*[_stream(s) for s in streams])
+    rc = lib().fc_solve_batched(count, H, R, Uc, O, infos, S)
+    for i in range(count):
+        us[i].rank = Uc[i].rank
+    if raise_on_fail or rc not in (FC_ENOCONV, FC_EBREAKDOWN, FC_ENAN):
+        _check("fc_solve_batched", rc)
+    return list(infos)
+
+
 def fc_to_full(h: Handle, x: CP, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """Full n^d array; returned with shape (n,)*d in numpy axis order (i_1 is axis 0)."""
     n, d = h.n, h.d
@@ -296,6 +325,20 @@ def fc_inner_static(x: CP, y: CP, out: torch.Tensor, stream=None) -> torch.Tenso
     _check("fc_inner_static", lib().fc_inner_static(C.byref(x.desc()), C.byref(y.desc()),
                                                     C.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+PROF_JACOBI = 1
+
+
+def fc_prof_enable(kclass: int) -> None:
+    _check("fc_prof_enable", lib().fc_prof_enable(int(kclass)))
+
+
+def fc_prof_read():
+    """(launches, summed event time in ms, algorithmic flops) of the instrumented class."""
+    n, ms, work = C.c_longlong(), C.c_double(), C.c_double()
+    _check("fc_prof_read", lib().fc_prof_read(C.byref(n), C.byref(ms), C.byref(work)))
+    return n.value, ms.value, work.value
 
 
 def fc_launch_count() -> int:

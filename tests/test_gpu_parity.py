@@ -292,3 +292,31 @@ def test_solve_config2_3d_n255(fc, problem):
     info, e = _solve_vs_full(fc, prob, prob.tol, prob.eps, max_rank=prob.max_rank)
     assert info.status == 0
     assert e < 1e-6
+
+
+def test_solve_batched_matches_independent_solves(fc):
+    """fc_solve_batched runs independent problems concurrently (one stream each); every
+    result equals the stand-alone fc_solve of the same problem within the solve accuracy,
+    and each solves its own equation (full oracle)."""
+    rng = np.random.default_rng(fi.seed_for(10))
+    probs = [fi.Problem(47, 3, a, 1.0, g, fi.gaussians_cp(47, 3, 3, rng), eps=1e-9, tol=1e-8,
+                        max_rank=96) for a, g in [(0.25, 1e-1), (0.5, 1e-3), (0.75, 1e-2)]]
+    hs = [fc.fc_setup(p.n, 3, p.alpha, 1.0, p.gamma, p.eps, max_rank=p.max_rank) for p in probs]
+    Bs = [fc.CP.from_factors(*p.rhs()) for p in probs]
+    Ub = [fc.CP(3, p.n, p.max_rank) for p in probs]
+    streams = [torch.cuda.Stream() for _ in probs]
+    infos = fc.fc_solve_batched(hs, Bs, Ub, streams, tol=[p.tol for p in probs],
+                                eps=[p.eps for p in probs])
+    torch.cuda.synchronize()
+    for p, h, B, U, info in zip(probs, hs, Bs, Ub, infos):
+        Us = fc.CP(3, p.n, p.max_rank)
+        fc.fc_solve(h, B, Us, tol=p.tol, eps=p.eps)
+        ub, us = gpu_full(fc, h, U), gpu_full(fc, h, Us)
+        ref = full.solve_full(cp.to_full(p.rhs()), p.alpha, 1.0, p.gamma)
+        print(f"batched a={p.alpha} g={p.gamma}: iters {info.iters} |b-s|={rel(ub, us):.2e} "
+              f"|b-full|={rel(ub, ref):.2e}")
+        assert info.status == 0
+        assert rel(ub, us) <= 1e-7
+        assert rel(ub, ref) <= 1e-6
+    with pytest.raises(fc.FCError):
+        fc.fc_solve_batched([hs[0], hs[0]], Bs[:2], Ub[:2], streams[:2])
