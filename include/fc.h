@@ -97,6 +97,9 @@ typedef struct fc_solve_info {
     int rank_x;         /* CP rank of the returned solution                                   */
     int max_rank_seen;  /* largest CP rank of any truncated iterate                           */
     int trunc_calls;
+    int tucker_max;     /* largest Tucker rank r_l chosen by any truncation of the solve      */
+    double tucker_mean; /* mean Tucker rank over all truncations and modes                    */
+    int basis_max;      /* largest orthonormal sketch basis (live columns) of any truncation */
     double history[128];/* relres per iteration (first min(iters,128))                       */
 } fc_solve_info;
 

@@ -126,6 +126,9 @@ struct fc_ctx {
         double* pinned_dummy;
     } w{};
     unsigned long long seed = 0x1809019710ull;
+    // rank statistics of the truncations since the last reset (fc_solve reports them)
+    long long stat_rsum = 0, stat_rcount = 0;
+    int stat_rmax = 0, stat_bmax = 0;
     // host pinned scalars for readback
     double* hbuf = nullptr;
     int* hint = nullptr;
@@ -382,6 +385,12 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     CK(cudaMemcpyAsync(h->hint, dims, sizeof(int) * D_SIZE, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     out.rank = h->hint[D_Q];
+    for (int l = 0; l < d; ++l) {
+        h->stat_rsum += h->hint[D_R + l];
+        h->stat_rcount += 1;
+        h->stat_rmax = std::max(h->stat_rmax, h->hint[D_R + l]);
+        h->stat_bmax = std::max(h->stat_bmax, h->hint[D_C1 + l]);
+    }
     return FC_OK;
 }
 
@@ -757,6 +766,8 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     if (rhs->rank > h->KIN) return FC_ERANK;
     fc_solve_info inf;
     std::memset(&inf, 0, sizeof(inf));
+    h->stat_rsum = h->stat_rcount = 0;
+    h->stat_rmax = h->stat_bmax = 0;
     cudaStream_t st = (cudaStream_t)stream;
     auto& w = h->w;
     CP B = from_user(rhs);
@@ -768,6 +779,9 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     auto finish = [&](int status) -> int {
         inf.status = status;
         inf.rank_x = X.rank;
+        inf.tucker_max = h->stat_rmax;
+        inf.basis_max = h->stat_bmax;
+        inf.tucker_mean = h->stat_rcount ? (double)h->stat_rsum / h->stat_rcount : 0.0;
         // copy X to the caller's u
         for (int l = 0; l < h->d; ++l)
             if (X.rank > 0)

@@ -60,6 +60,7 @@ class fc_solve_opts(C.Structure):
 class fc_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("relres", C.c_double),
                 ("rank_x", C.c_int), ("max_rank_seen", C.c_int), ("trunc_calls", C.c_int),
+                ("tucker_max", C.c_int), ("tucker_mean", C.c_double), ("basis_max", C.c_int),
                 ("history", C.c_double * 128)]
 
 
