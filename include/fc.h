@@ -207,10 +207,19 @@ const char* fc_last_cuda_error(void);
  * devices); a host-side counter for instrumentation, no synchronisation. */
 unsigned long long fc_launch_count(void);
 
+/* Eigen-decomposition of `batch` symmetric m x m FP64 matrices on the device (m <= 64): the
+ * dense eigen-solver the RHOSVD truncation uses for its small Gram matrices (Section 5).
+ * Matrix b is column-major at dev_A + b*strideA (leading dimension lda; its symmetric part is
+ * used); eigenvalues in descending order go to dev_w + b*strideW, orthonormal eigenvectors to
+ * the columns of dev_V + b*strideV (leading dimension ldv).  Householder tridiagonalisation,
+ * bisection, inverse iteration, back-transformation; one CTA per matrix.  Stream-ordered. */
+int fc_symeig(int batch, int m, const double* dev_A, int lda, long long strideA, double* dev_w,
+              long long strideW, double* dev_V, int ldv, long long strideV, void* stream);
+
 /* Kernel-class instrumentation.  fc_prof_enable(kclass) synchronises the device, clears the
  * counters and, until fc_prof_read, brackets every launch of that class with a pair of CUDA
  * events on its stream and accumulates the class's algorithmic work on the device.
- * kclass: 0 = off, 1 = the FP64 Jacobi eigensolver (work = 9 c^3 flops per c x c matrix).
+ * kclass: 0 = off, 1 = the FP64 small eigen-solver (work = 9 c^3 flops per c x c matrix).
  * fc_prof_read disables it, synchronises, and returns the launches, the summed event time of
  * those launches in ms, and the work (flops). */
 int fc_prof_enable(int kclass);

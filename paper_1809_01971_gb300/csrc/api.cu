@@ -188,6 +188,22 @@ size_t layout(fc_ctx* h, Arena& a) {
     return a.off + 256;
 }
 
+// Kernel attributes are per device: set them once for every device the library runs on.
+int ensure_attributes() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FC_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        cudaError_t e = set_linalg_attributes();
+        if (e == cudaSuccess) e = set_symeig_attributes();
+        if (e != cudaSuccess) return cuda_fail(e);
+        done[dev] = true;
+    }
+    return FC_OK;
+}
+
 CP from_user(const fc_cp* x) {
     CP c;
     c.rank = x->rank; c.cap = x->cap; c.ld = x->ld; c.xi = x->xi;
@@ -319,7 +335,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         launch_sumsq(st, (int)K, dn->w, w.scal + 4, 1);
     }
     CKL();
-    launch_jacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC);
+    launch_symeig(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC);
     // Zc_l = Q_l Vr_l (all cs Ritz directions, descending)
     gemm(st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
     // B2_l = Zc_l^T U_l (cs x K, unweighted): its first r_l rows are the projected factors C_l
@@ -354,13 +370,13 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     // mode-3 rotation: G3 = B3^T B3, W3 = eigvecs, Srot = B3 W3
     gemm(st, RM, RM, RR, LdT{w.core, RR, 0}, LdN{w.core, RR, 0}, 1.0, 0.0, w.G3, RM, 0, 1,
          dims + D_R3, dims + D_R3, dims + D_R12);
-    launch_jacobi(st, 1, w.G3, RM, 0, dims + D_R3, 0, RM, w.ev3, 0, w.W3, RM, 0);
+    launch_symeig(st, 1, w.G3, RM, 0, dims + D_R3, 0, RM, w.ev3, 0, w.W3, RM, 0);
     gemm(st, RR, RM, RM, LdN{w.core, RR, 0}, LdN{w.W3, RM, 0}, 1.0, 0.0, w.Srot, RR, 0, 1,
          dims + D_R12, dims + D_R3, dims + D_R3);
     // slice Grams SG[s] = S_s^T S_s  (S_s = r0 x r1, compact column s of Srot)
     gemm(st, RM, RM, RM, LdSlT{w.Srot, RR, dims + D_R}, LdSl{w.Srot, RR, dims + D_R}, 1.0, 0.0,
          w.SG, RM, RR, (d == 3) ? RM : 1, dims + D_R + 1, dims + D_R + 1, dims + D_R);
-    launch_jacobi(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR);
+    launch_symeig(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR);
     // candidate term energies ||S_s y_i||^2 taken directly (not the Gram eigenvalues)
     launch_slice_energy(st, (d == 3) ? RM : 1, RM, dims, w.Srot, RR, w.Vs, RM, RR, w.mus, RM);
     CKL();
@@ -473,6 +489,19 @@ const char* fc_strerror(int code) {
 
 const char* fc_last_cuda_error(void) { return g_cuda_msg.c_str(); }
 
+int fc_symeig(int batch, int m, const double* dev_A, int lda, long long strideA, double* dev_w,
+              long long strideW, double* dev_V, int ldv, long long strideV, void* stream) {
+    if (batch < 0 || m < 0 || m > kMaxC || (batch > 0 && m > 0 && (!dev_A || !dev_w || !dev_V)) ||
+        lda < m || ldv < m)
+        return FC_EINVAL;
+    if (batch == 0 || m == 0) return FC_OK;
+    if (int rc = ensure_attributes()) return rc;
+    launch_symeig((cudaStream_t)stream, batch, dev_A, lda, strideA, nullptr, 0, m, dev_w, strideW,
+                  dev_V, ldv, strideV);
+    CKL();
+    return FC_OK;
+}
+
 int fc_prof_enable(int kclass) {
     if (kclass < 0 || kclass > KC_JACOBI) return FC_EINVAL;
     std::lock_guard<std::mutex> lock(g_prof_mu);
@@ -528,19 +557,7 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     opts.max_tucker = std::min(opts.max_tucker, kMaxC - 8);
     opts.max_rank = std::min(opts.max_rank, opts.max_tucker * opts.max_tucker);
     if (opts.max_input_rank <= 0) opts.max_input_rank = opts.max_rank;
-    {
-        // kernel attributes are per device: set them once for every device a handle uses
-        static std::mutex mu;
-        static bool done[64] = {false};
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FC_ECUDA;
-        std::lock_guard<std::mutex> lock(mu);
-        if (!done[dev]) {
-            cudaError_t e = set_linalg_attributes();
-            if (e != cudaSuccess) return cuda_fail(e);
-            done[dev] = true;
-        }
-    }
+    if (int rc_ = ensure_attributes()) return rc_;
     SymbolNodes sym, pc;
     if (!build_control_nodes(n, d, alpha, beta, gamma, opts.delta_sym, sym)) return FC_ESETUP;
     if (!build_precond_nodes(n, d, alpha, beta, gamma, opts.precond_rank, pc)) return FC_ESETUP;

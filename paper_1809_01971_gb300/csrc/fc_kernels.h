@@ -8,6 +8,15 @@ namespace fc {
 // ---- k_linalg.cu ---------------------------------------------------------------------
 size_t jacobi_smem(int cmax);
 size_t pchol_smem();
+// ---- k_symeig.cu ------------------------------------------------------------------------
+// Same contract as launch_jacobi: item b is the symmetric c x c matrix at A + b*bsA with
+// c = dims ? min(dims[b*dstride], cmax) : cmax; eigenvalues descending into ev + b*bsE,
+// orthonormal eigenvectors as columns of V + b*bsV (cmax x cmax, zero-padded).
+void launch_symeig(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
+                   const int* dims, int dstride, int cmax, double* ev, long long bsE,
+                   double* V, int ldv, long long bsV);
+size_t symeig_smem();
+cudaError_t set_symeig_attributes();
 // Opt the large-shared-memory kernels in to their dynamic shared memory (per device).
 cudaError_t set_linalg_attributes();
 void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,

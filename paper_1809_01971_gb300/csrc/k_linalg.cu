@@ -9,11 +9,6 @@
 
 namespace fc {
 
-// Algorithmic work counter of the instrumented kernel class (see prof_* in api.cu):
-// a symmetric eigen-decomposition with eigenvectors counts 9 c^3 flops (Householder
-// tridiagonalisation + implicit QR with accumulation, the textbook figure).
-__device__ unsigned long long g_prof_work = 0;
-
 // ---------------------------------------------------------------------------------------
 // Jacobi eigen-decomposition.  Item b: symmetric c x c matrix at A + b*bsA (ld lda),
 // c = dims ? min(dims[b*dstride], cmax) : cmax.  Writes eigenvalues in descending order to
@@ -32,8 +27,7 @@ jacobi_eig_kernel(const double* __restrict__ A, int lda, long long bsA,
     int c = cmax;
     if (dims) c = min(dims[b * dstride], cmax);
     if (c < 0) c = 0;
-    if (prof && threadIdx.x == 0)
-        atomicAdd(&g_prof_work, 9ull * (unsigned long long)c * c * c);
+    (void)prof;
     const int m = (c + 1) & ~1;           // even number of players
     const int S = m + 1;                  // smem row stride
     double* a = sm;                       // m x S
@@ -164,19 +158,8 @@ void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long lo
 {
     if (batch <= 0) return;
     size_t sm = jacobi_smem(cmax);
-    const bool prof = prof_active(KC_JACOBI);
-    ProfMark mark;
-    if (prof) prof_begin(st, mark);
     note_launch(); jacobi_eig_kernel<<<batch, 256, sm, st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv,
-                                               bsV, 30, prof ? 1 : 0);
-    if (prof) prof_end(st, mark);
-}
-
-unsigned long long* prof_work_counter()
-{
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_prof_work) != cudaSuccess) return nullptr;
-    return static_cast<unsigned long long*>(p);
+                                               bsV, 30, 0);
 }
 
 // ---------------------------------------------------------------------------------------

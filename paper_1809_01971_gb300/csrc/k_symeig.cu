@@ -1,0 +1,359 @@
+// Symmetric eigen-decomposition of small FP64 matrices (m <= kMaxC = 64), one CTA per matrix.
+// It orders the bases of the RHOSVD truncation (Section 5): the Rayleigh-Ritz matrix of the
+// sketched side matrices, the mode-3 Gram of the Tucker core and the core slices' Grams.
+//
+// Steps (textbook dense symmetric eigen-solver, Golub & Van Loan Ch. 8):
+//   1. Householder tridiagonalisation A = Q T Q^T; the reflectors stay in A's lower triangle.
+//   2. Eigenvalues of T by bisection on Sturm-sequence counts, one thread per eigenvalue; the
+//      brackets come from counts on a geometric grid of 256 points (one per thread).
+//   3. Eigenvectors of T by inverse iteration (tridiagonal LU with partial pivoting), one
+//      thread per eigenvector, then Gram-Schmidt (two passes) in order of decreasing
+//      eigenvalue, so that vectors of close eigenvalues come out orthonormal.
+//   4. Back-transformation V = Q Z.
+// The matrix is scaled to unit Frobenius norm first, which keeps the Sturm recurrence in
+// range and makes all tolerances absolute.  Flops ~ (4/3 + 2 + 2) m^3 against ~100 m^3 for a
+// cyclic Jacobi solve; on GB300 (2 FP64 FMA per clock per SM) that is what decides the time.
+// Eigenvalues are accurate to ~u ||A|| in absolute terms (as for any backward-stable method);
+// the eigenvectors are orthonormal to ~u.
+#include "fc_common.cuh"
+#include "fc_kernels.h"
+
+namespace fc {
+
+// Algorithmic work of the instrumented eigen-solves (fc_prof_*): a symmetric eigen-
+// decomposition with eigenvectors counts 9 m^3 flops (the textbook dense figure).
+__device__ unsigned long long g_prof_work = 0;
+
+unsigned long long* prof_work_counter()
+{
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_prof_work) != cudaSuccess) return nullptr;
+    return static_cast<unsigned long long*>(p);
+}
+
+namespace {
+
+constexpr int kEigThreads = 256;
+constexpr int kGrid = 256;            // bracket grid: one Sturm count per thread
+constexpr double kTolAbs = 4e-16;     // bisection stops at this width (matrix scaled to norm 1)
+
+FC_DEV bool neg(double x) { return __double_as_longlong(x) < 0; }
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below sigma: sign changes of the
+// Sturm sequence p_0 = 1, p_1 = d_0 - sigma, p_k = (d_{k-1} - sigma) p_{k-1} - e_{k-2}^2 p_{k-2}
+// (a zero term takes the sign opposite to its predecessor).  With ||T|| <= 1 a term grows by at
+// most 3x per step, so only underflow needs guarding: every 8 steps the pair is rescaled.
+FC_DEV int sturm_below(const double* d, const double* e2, int m, double sigma) {
+    double pm2 = 1.0, pm1 = d[0] - sigma;
+    if (pm1 == 0.0) pm1 = -1e-300;
+    int cnt = neg(pm1);
+    for (int k = 1; k < m; ++k) {
+        double p = fma(d[k] - sigma, pm1, -e2[k - 1] * pm2);
+        if ((__double_as_longlong(p) << 1) == 0) p = neg(pm1) ? 1e-300 : -1e-300;
+        cnt += (neg(p) != neg(pm1));
+        if ((k & 7) == 0) {
+            int ex = (int)((__double_as_longlong(p) >> 52) & 0x7ff);
+            if (ex < 1023 - 300) { p *= 0x1p+600; pm1 *= 0x1p+600; }
+        }
+        pm2 = pm1;
+        pm1 = p;
+    }
+    return cnt;
+}
+
+// x <- (T - lam I)^-1 x for the tridiagonal (d, e) (x in shared memory, stride xs), by an LU
+// factorisation with partial pivoting computed once per call; pivots below tol are replaced
+// by +-tol.  u0/u1/u2: the three diagonals of U (u0 stored inverted), l: multipliers,
+// sw: row swap at step k.
+struct TriLU {
+    double u0[kMaxC], u1[kMaxC], u2[kMaxC], l[kMaxC];
+    unsigned char sw[kMaxC];
+};
+
+FC_DEV void tri_factor(const double* d, const double* e, int m, double lam, double tol, TriLU& f) {
+    double a = d[0] - lam, c = (m > 1) ? e[0] : 0.0, g = 0.0;
+    for (int k = 0; k + 1 < m; ++k) {
+        const double b = e[k], a1 = d[k + 1] - lam, c1 = (k + 2 < m) ? e[k + 1] : 0.0;
+        if (fabs(a) >= fabs(b)) {
+            if (fabs(a) < tol) a = neg(a) ? -tol : tol;
+            const double mult = b / a;
+            f.u0[k] = 1.0 / a; f.u1[k] = c; f.u2[k] = g; f.l[k] = mult; f.sw[k] = 0;
+            a = a1 - mult * c;
+            c = c1 - mult * g;
+            g = 0.0;
+        } else {
+            const double mult = a / b;
+            f.u0[k] = 1.0 / b; f.u1[k] = a1; f.u2[k] = c1; f.l[k] = mult; f.sw[k] = 1;
+            const double na = c - mult * a1, nc = g - mult * c1;
+            a = na;
+            c = nc;
+            g = 0.0;
+        }
+    }
+    if (fabs(a) < tol) a = neg(a) ? -tol : tol;
+    f.u0[m - 1] = 1.0 / a;
+}
+
+FC_DEV void tri_solve(const TriLU& f, int m, double* x, int xs) {
+    for (int k = 0; k + 1 < m; ++k) {
+        if (f.sw[k]) { double t = x[k * xs]; x[k * xs] = x[(k + 1) * xs]; x[(k + 1) * xs] = t; }
+        x[(k + 1) * xs] -= f.l[k] * x[k * xs];
+    }
+    x[(m - 1) * xs] *= f.u0[m - 1];
+    if (m >= 2) x[(m - 2) * xs] = (x[(m - 2) * xs] - f.u1[m - 2] * x[(m - 1) * xs]) * f.u0[m - 2];
+    for (int k = m - 3; k >= 0; --k)
+        x[k * xs] = (x[k * xs] - f.u1[k] * x[(k + 1) * xs] - f.u2[k] * x[(k + 2) * xs]) * f.u0[k];
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kEigThreads)
+symeig_kernel(const double* __restrict__ A, int lda, long long bsA, const int* __restrict__ dims,
+              int dstride, int cmax, double* __restrict__ ev, long long bsE,
+              double* __restrict__ V, int ldv, long long bsV, int prof)
+{
+    extern __shared__ double sm[];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    int m = cmax;
+    if (dims) m = min(dims[b * dstride], cmax);
+    if (m < 0) m = 0;
+    if (prof && tid == 0) atomicAdd(&g_prof_work, 9ull * (unsigned long long)m * m * m);
+    const int S = kMaxC + 1;
+    double* a = sm;                      // m x S, row-major: a[i*S + j]
+    double* z = a + kMaxC * S;           // eigenvectors of T, column c = eigenvalue rank c
+    double* d = z + kMaxC * S;
+    double* e = d + kMaxC;
+    double* e2 = e + kMaxC;
+    double* tau = e2 + kMaxC;
+    double* lam = tau + kMaxC;           // ascending
+    double* wv = lam + kMaxC;            // work vector (p / w of the reflector update)
+    double* coef = wv + kMaxC;           // Gram-Schmidt coefficients
+    double* gpt = coef + kMaxC;          // grid points (kGrid)
+    int* gcnt = (int*)(gpt + kGrid);     // counts at the grid points
+    __shared__ double red[32];
+    __shared__ double sh_scal[4];
+
+    const double* Ab = A + b * bsA;
+    double* evb = ev + b * bsE;
+    double* Vb = V + b * bsV;
+    for (int e_ = tid; e_ < cmax * cmax; e_ += blockDim.x) Vb[(e_ % cmax) + (long long)(e_ / cmax) * ldv] = 0.0;
+    for (int i = tid; i < cmax; i += blockDim.x) evb[i] = 0.0;
+    if (m == 0) return;
+
+    // ---- load (symmetrised) and scale to unit Frobenius norm -----------------------------
+    double fro = 0.0;
+    for (int e_ = tid; e_ < m * m; e_ += blockDim.x) {
+        int i = e_ % m, j = e_ / m;
+        double x = 0.5 * (Ab[i + (long long)j * lda] + Ab[j + (long long)i * lda]);
+        a[i * S + j] = x;
+        fro += x * x;
+    }
+    fro = sqrt(block_sum(fro, red));
+    if (!(fro > 0.0) || !isfinite(fro)) {
+        // zero (or non-finite) matrix: eigenvalues 0, V = I
+        __syncthreads();
+        for (int i = tid; i < m; i += blockDim.x) Vb[i + (long long)i * ldv] = 1.0;
+        return;
+    }
+    const double inv = 1.0 / fro;
+    for (int e_ = tid; e_ < m * m; e_ += blockDim.x) a[(e_ / m) * S + (e_ % m)] *= inv;
+    __syncthreads();
+
+    // ---- 1. Householder tridiagonalisation ------------------------------------------------
+    for (int k = 0; k + 2 < m; ++k) {
+        const int L = m - k - 1;                        // rows k+1 .. m-1
+        double s = 0.0;
+        for (int i = 1 + tid; i < L; i += blockDim.x) { double x = a[(k + 1 + i) * S + k]; s += x * x; }
+        const double sigma = block_sum(s, red);
+        const double alpha = a[(k + 1) * S + k];
+        if (tid == 0) {
+            d[k] = a[k * S + k];
+            if (sigma == 0.0) {
+                tau[k] = 0.0;
+                e[k] = alpha;
+                sh_scal[0] = 0.0;
+            } else {
+                const double mu = sqrt(alpha * alpha + sigma);
+                const double beta = (alpha <= 0.0) ? mu : -mu;
+                tau[k] = (beta - alpha) / beta;
+                e[k] = beta;
+                sh_scal[0] = 1.0 / (alpha - beta);
+            }
+        }
+        __syncthreads();
+        const double t = tau[k];
+        if (t == 0.0) continue;
+        const double sc = sh_scal[0];
+        for (int i = 1 + tid; i < L; i += blockDim.x) a[(k + 1 + i) * S + k] *= sc;
+        if (tid == 0) a[(k + 1) * S + k] = 1.0;
+        __syncthreads();
+        // p = t A22 v ; K = t/2 v^T p ; w = p - K v ; A22 -= v w^T + w v^T
+        double kk = 0.0;
+        for (int r = tid; r < L; r += blockDim.x) {
+            double acc = 0.0;
+            const double* row = a + (k + 1 + r) * S + (k + 1);
+            for (int c = 0; c < L; ++c) acc = fma(row[c], a[(k + 1 + c) * S + k], acc);
+            acc *= t;
+            wv[r] = acc;
+            kk += acc * a[(k + 1 + r) * S + k];
+        }
+        const double K = 0.5 * t * block_sum(kk, red);
+        for (int r = tid; r < L; r += blockDim.x) wv[r] -= K * a[(k + 1 + r) * S + k];
+        __syncthreads();
+        for (int e_ = tid; e_ < L * L; e_ += blockDim.x) {
+            const int r = e_ / L, c = e_ - r * L;
+            const double vr = a[(k + 1 + r) * S + k], vc = a[(k + 1 + c) * S + k];
+            a[(k + 1 + r) * S + (k + 1 + c)] -= vr * wv[c] + wv[r] * vc;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (m >= 2) {
+            d[m - 2] = a[(m - 2) * S + (m - 2)];
+            e[m - 2] = a[(m - 1) * S + (m - 2)];
+            tau[m - 2] = 0.0;
+        }
+        d[m - 1] = a[(m - 1) * S + (m - 1)];
+        e[m - 1] = 0.0;
+        tau[m - 1] = 0.0;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) e2[i] = e[i] * e[i];
+    __syncthreads();
+
+    // ---- 2. eigenvalues: grid of counts, then bisection per eigenvalue ---------------------
+    // grid: +-10^(-g/8), g = 0..127 (covers the scaled spectrum [-1, 1] down to 1e-16)
+    {
+        const int g = tid;
+        double x = exp10(-(double)(g & 127) / 8.0);
+        if (g >= 128) x = -x;
+        gpt[g] = x;
+        gcnt[g] = sturm_below(d, e2, m, x);
+    }
+    __syncthreads();
+    const int c0 = sturm_below(d, e2, m, 0.0);    // eigenvalues below 0 (computed redundantly)
+    if (tid < m) {
+        const int j = tid;                          // j-th smallest eigenvalue
+        double lo = -1.0000001, hi = 1.0000001;     // |lambda| <= ||T||_F = 1
+        if (j < c0) hi = 0.0; else lo = 0.0;
+        for (int g = 0; g < kGrid; ++g) {
+            const double x = gpt[g];
+            const int cnt = gcnt[g];
+            if (cnt <= j && x > lo) lo = x;         // at most j eigenvalues below x
+            if (cnt > j && x < hi) hi = x;
+        }
+        for (int it = 0; it < 80 && hi - lo > kTolAbs; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (sturm_below(d, e2, m, mid) > j) hi = mid; else lo = mid;
+        }
+        lam[j] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+
+    // ---- 3. eigenvectors of T: inverse iteration, then Gram-Schmidt ----------------------
+    // column c of z holds the eigenvector of the c-th largest eigenvalue
+    if (tid < m) {
+        const int j = tid, c = m - 1 - j;
+        TriLU f;
+        tri_factor(d, e, m, lam[j], 4e-16, f);
+        double* x = z + c;
+        unsigned int h = 0x9E3779B9u * (unsigned)(j + 1);
+        for (int i = 0; i < m; ++i) {
+            h ^= h << 13; h ^= h >> 17; h ^= h << 5;
+            x[i * S] = 1.0 + 0.25 * ((double)(h & 0xffff) / 65536.0 - 0.5);
+        }
+        for (int it = 0; it < 3; ++it) {
+            tri_solve(f, m, x, S);
+            double mx = 0.0;
+            for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(x[i * S]));
+            const double s_ = (mx > 0.0 && isfinite(mx)) ? 1.0 / mx : 0.0;
+            for (int i = 0; i < m; ++i) x[i * S] *= s_;
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < m; ++c) {
+        // two classical Gram-Schmidt passes against columns 0..c-1, then normalise; a column
+        // that vanishes (repeated eigenvalue) is replaced by unit vectors until one survives
+        for (int attempt = 0; attempt <= m; ++attempt) {
+            double n0 = 0.0;
+            for (int i = tid; i < m; i += blockDim.x) n0 += z[i * S + c] * z[i * S + c];
+            n0 = block_sum(n0, red);
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int q = tid; q < c; q += blockDim.x) {
+                    double s_ = 0.0;
+                    for (int i = 0; i < m; ++i) s_ = fma(z[i * S + q], z[i * S + c], s_);
+                    coef[q] = s_;
+                }
+                __syncthreads();
+                for (int i = tid; i < m; i += blockDim.x) {
+                    double s_ = z[i * S + c];
+                    for (int q = 0; q < c; ++q) s_ = fma(-coef[q], z[i * S + q], s_);
+                    z[i * S + c] = s_;
+                }
+                __syncthreads();
+            }
+            double n1 = 0.0;
+            for (int i = tid; i < m; i += blockDim.x) n1 += z[i * S + c] * z[i * S + c];
+            n1 = block_sum(n1, red);
+            if (n1 > 1e-6 * n0 && n1 > 0.0 && isfinite(n1)) {
+                const double s_ = 1.0 / sqrt(n1);
+                for (int i = tid; i < m; i += blockDim.x) z[i * S + c] *= s_;
+                __syncthreads();
+                break;
+            }
+            // replace by the unit vector e_((c + attempt) mod m) and orthogonalise again
+            for (int i = tid; i < m; i += blockDim.x) z[i * S + c] = (i == (c + attempt) % m) ? 1.0 : 0.0;
+            __syncthreads();
+        }
+    }
+
+    // ---- 4. back-transformation V = H_0 H_1 ... H_{m-3} Z --------------------------------
+    for (int k = m - 3; k >= 0; --k) {
+        const double t = tau[k];
+        if (t == 0.0) continue;                      // uniform across the block
+        const int L = m - k - 1;
+        for (int c = tid; c < m; c += blockDim.x) {
+            double s_ = 0.0;
+            for (int i = 0; i < L; ++i) s_ = fma(a[(k + 1 + i) * S + k], z[(k + 1 + i) * S + c], s_);
+            coef[c] = t * s_;
+        }
+        __syncthreads();
+        for (int e_ = tid; e_ < L * m; e_ += blockDim.x) {
+            const int i = e_ / m, c = e_ - i * m;
+            z[(k + 1 + i) * S + c] -= a[(k + 1 + i) * S + k] * coef[c];
+        }
+        __syncthreads();
+    }
+
+    // ---- outputs: eigenvalues descending (unscaled), eigenvectors as columns -------------
+    for (int c = tid; c < m; c += blockDim.x) evb[c] = fro * lam[m - 1 - c];
+    for (int e_ = tid; e_ < m * m; e_ += blockDim.x) {
+        const int i = e_ % m, c = e_ / m;
+        Vb[i + (long long)c * ldv] = z[i * S + c];
+    }
+}
+
+size_t symeig_smem() {
+    const int S = kMaxC + 1;
+    return sizeof(double) * (2 * (size_t)kMaxC * S + 7 * kMaxC + kGrid) + sizeof(int) * kGrid;
+}
+
+void launch_symeig(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
+                   const int* dims, int dstride, int cmax, double* ev, long long bsE,
+                   double* V, int ldv, long long bsV)
+{
+    if (batch <= 0) return;
+    const bool prof = prof_active(KC_JACOBI);
+    ProfMark mark;
+    if (prof) prof_begin(st, mark);
+    note_launch(); symeig_kernel<<<batch, kEigThreads, symeig_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, prof ? 1 : 0);
+    if (prof) prof_end(st, mark);
+}
+
+cudaError_t set_symeig_attributes()
+{
+    return cudaFuncSetAttribute(symeig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)symeig_smem());
+}
+
+}  // namespace fc
