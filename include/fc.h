@@ -207,14 +207,20 @@ const char* fc_last_cuda_error(void);
  * devices); a host-side counter for instrumentation, no synchronisation. */
 unsigned long long fc_launch_count(void);
 
-/* Eigen-decomposition of `batch` symmetric m x m FP64 matrices on the device (m <= 64): the
- * dense eigen-solver the RHOSVD truncation uses for its small Gram matrices (Section 5).
- * Matrix b is column-major at dev_A + b*strideA (leading dimension lda; its symmetric part is
- * used); eigenvalues in descending order go to dev_w + b*strideW, orthonormal eigenvectors to
- * the columns of dev_V + b*strideV (leading dimension ldv).  Householder tridiagonalisation,
- * bisection, inverse iteration, back-transformation; one CTA per matrix.  Stream-ordered. */
-int fc_symeig(int batch, int m, const double* dev_A, int lda, long long strideA, double* dev_w,
-              long long strideW, double* dev_V, int ldv, long long strideV, void* stream);
+/* Eigen-decomposition of `batch` symmetric m x m FP64 matrices on the device (m <= 64), the
+ * small dense eigen-solves of the RHOSVD truncation (Section 5).  Matrix b is column-major at
+ * dev_A + b*strideA (leading dimension lda; its symmetric part is used); eigenvalues in
+ * descending order go to dev_w + b*strideW, orthonormal eigenvectors to the columns of
+ * dev_V + b*strideV (leading dimension ldv).  One CTA per matrix; stream-ordered.
+ *  method 0: Householder tridiagonalisation, bisection, inverse iteration, back-transformation
+ *            (FP64, eigenvalues accurate to ~u ||A|| in absolute terms);
+ *  method 1: the truncation's solver for graded positive semi-definite Grams: Jacobi sweeps in
+ *            FP32, eigenvectors made orthonormal in FP64 (to ~u) by Cholesky-QR in order of
+ *            increasing eigenvalue; eigen-directions accurate relative to the grading, the
+ *            eigenvalues FP64 Rayleigh quotients of the returned vectors. */
+int fc_symeig(int method, int batch, int m, const double* dev_A, int lda, long long strideA,
+              double* dev_w, long long strideW, double* dev_V, int ldv, long long strideV,
+              void* stream);
 
 /* Kernel-class instrumentation.  fc_prof_enable(kclass) synchronises the device, clears the
  * counters and, until fc_prof_read, brackets every launch of that class with a pair of CUDA

@@ -335,7 +335,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         launch_sumsq(st, (int)K, dn->w, w.scal + 4, 1);
     }
     CKL();
-    launch_symeig(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC);
+    launch_gjacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC, false);
     // Zc_l = Q_l Vr_l (all cs Ritz directions, descending)
     gemm(st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
     // B2_l = Zc_l^T U_l (cs x K, unweighted): its first r_l rows are the projected factors C_l
@@ -370,13 +370,13 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     // mode-3 rotation: G3 = B3^T B3, W3 = eigvecs, Srot = B3 W3
     gemm(st, RM, RM, RR, LdT{w.core, RR, 0}, LdN{w.core, RR, 0}, 1.0, 0.0, w.G3, RM, 0, 1,
          dims + D_R3, dims + D_R3, dims + D_R12);
-    launch_symeig(st, 1, w.G3, RM, 0, dims + D_R3, 0, RM, w.ev3, 0, w.W3, RM, 0);
+    launch_gjacobi(st, 1, w.G3, RM, 0, dims + D_R3, 0, RM, w.ev3, 0, w.W3, RM, 0, false);
     gemm(st, RR, RM, RM, LdN{w.core, RR, 0}, LdN{w.W3, RM, 0}, 1.0, 0.0, w.Srot, RR, 0, 1,
          dims + D_R12, dims + D_R3, dims + D_R3);
     // slice Grams SG[s] = S_s^T S_s  (S_s = r0 x r1, compact column s of Srot)
     gemm(st, RM, RM, RM, LdSlT{w.Srot, RR, dims + D_R}, LdSl{w.Srot, RR, dims + D_R}, 1.0, 0.0,
          w.SG, RM, RR, (d == 3) ? RM : 1, dims + D_R + 1, dims + D_R + 1, dims + D_R);
-    launch_symeig(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR);
+    launch_gjacobi(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR, false);
     // candidate term energies ||S_s y_i||^2 taken directly (not the Gram eigenvalues)
     launch_slice_energy(st, (d == 3) ? RM : 1, RM, dims, w.Srot, RR, w.Vs, RM, RR, w.mus, RM);
     CKL();
@@ -489,15 +489,20 @@ const char* fc_strerror(int code) {
 
 const char* fc_last_cuda_error(void) { return g_cuda_msg.c_str(); }
 
-int fc_symeig(int batch, int m, const double* dev_A, int lda, long long strideA, double* dev_w,
-              long long strideW, double* dev_V, int ldv, long long strideV, void* stream) {
-    if (batch < 0 || m < 0 || m > kMaxC || (batch > 0 && m > 0 && (!dev_A || !dev_w || !dev_V)) ||
-        lda < m || ldv < m)
+int fc_symeig(int method, int batch, int m, const double* dev_A, int lda, long long strideA,
+              double* dev_w, long long strideW, double* dev_V, int ldv, long long strideV,
+              void* stream) {
+    if (!(method == 0 || method == 1) || batch < 0 || m < 0 || m > kMaxC ||
+        (batch > 0 && m > 0 && (!dev_A || !dev_w || !dev_V)) || lda < m || ldv < m)
         return FC_EINVAL;
     if (batch == 0 || m == 0) return FC_OK;
     if (int rc = ensure_attributes()) return rc;
-    launch_symeig((cudaStream_t)stream, batch, dev_A, lda, strideA, nullptr, 0, m, dev_w, strideW,
-                  dev_V, ldv, strideV);
+    if (method == 0)
+        launch_symeig((cudaStream_t)stream, batch, dev_A, lda, strideA, nullptr, 0, m, dev_w,
+                      strideW, dev_V, ldv, strideV);
+    else
+        launch_gjacobi((cudaStream_t)stream, batch, dev_A, lda, strideA, nullptr, 0, m, dev_w,
+                       strideW, dev_V, ldv, strideV, true);
     CKL();
     return FC_OK;
 }

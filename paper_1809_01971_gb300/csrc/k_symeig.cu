@@ -333,6 +333,242 @@ symeig_kernel(const double* __restrict__ A, int lda, long long bsA, const int* _
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Graded eigen-solver for the truncation: cyclic Jacobi sweeps in FP32 on the matrix scaled
+// by its largest diagonal entry, then FP64 orthonormalisation of the eigenvectors.
+//
+// The RHOSVD's Gram matrices are graded (their basis comes from a pivoted Cholesky-QR, so the
+// diagonal falls from ~1 to ~1e-18); two-sided Jacobi determines the eigen-directions of a
+// graded positive definite matrix to high *relative* accuracy, entry by entry (Demmel and
+// Veselic, 1992), which Householder reduction does not: with Householder the small
+// directions mix and the truncation keeps up to all sketch columns, with Jacobi it reaches
+// the optimal rank.  FP32 keeps that grading (it stores each entry with 1e-7 relative
+// precision) at 64x GB300's FP64 rate; the eigenvectors are then made orthonormal to FP64
+// precision by Cholesky-QR taken in order of *increasing* eigenvalue, so a direction only
+// ever absorbs components of smaller ones (never a large one leaking into a small one).
+// Eigenvalues: FP64 Rayleigh quotients of the final vectors if `rq`, else the FP32 values.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kEigThreads)
+gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* __restrict__ dims,
+               int dstride, int cmax, double* __restrict__ ev, long long bsE,
+               double* __restrict__ V, int ldv, long long bsV, int rq, int prof)
+{
+    extern __shared__ double sm[];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    int c = cmax;
+    if (dims) c = min(dims[b * dstride], cmax);
+    if (c < 0) c = 0;
+    if (prof && tid == 0) atomicAdd(&g_prof_work, 9ull * (unsigned long long)c * c * c);
+    const int S = kMaxC + 1;
+    double* A64 = sm;                      // c x S
+    double* V64 = A64 + kMaxC * S;         // c x S
+    double* G = V64 + kMaxC * S;           // c x S (Gram / Cholesky factor)
+    float* a = (float*)(G + kMaxC * S);    // m x S (FP32 working matrix)
+    float* v = a + kMaxC * S;              // m x S (FP32 eigenvectors, row-major v[r*S+col])
+    float* coefS = v + kMaxC * S;
+    float* coefP = coefS + kMaxC;
+    int* partner = (int*)(coefP + kMaxC);
+    int* rotated = partner + kMaxC;
+    int* order = rotated + kMaxC;          // ascending eigenvalue order
+    __shared__ double red[32];
+    __shared__ int anyRot;
+
+    const double* Ab = A + b * bsA;
+    double* evb = ev + b * bsE;
+    double* Vb = V + b * bsV;
+    for (int e_ = tid; e_ < cmax * cmax; e_ += blockDim.x) Vb[(e_ % cmax) + (long long)(e_ / cmax) * ldv] = 0.0;
+    for (int i = tid; i < cmax; i += blockDim.x) evb[i] = 0.0;
+    if (c == 0) return;
+    const int m = (c + 1) & ~1;           // even number of players (padded with a zero row)
+
+    double dmax = 0.0;
+    for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
+        const int i = e_ % c, j = e_ / c;
+        const double x = 0.5 * (Ab[i + (long long)j * lda] + Ab[j + (long long)i * lda]);
+        A64[i * S + j] = x;
+        if (i == j) dmax = fmax(dmax, fabs(x));
+    }
+    dmax = warp_max(dmax);
+    if ((tid & 31) == 0) red[tid >> 5] = dmax;
+    __syncthreads();
+    if (tid < 32) {
+        double t = (tid < (int)(blockDim.x >> 5)) ? red[tid] : 0.0;
+        t = warp_max(t);
+        if (tid == 0) red[0] = t;
+    }
+    __syncthreads();
+    dmax = red[0];
+    __syncthreads();
+    if (!(dmax > 0.0) || !isfinite(dmax)) {
+        for (int i = tid; i < c; i += blockDim.x) Vb[i + (long long)i * ldv] = 1.0;
+        return;
+    }
+    const double sc = 1.0 / dmax;
+    for (int e_ = tid; e_ < m * m; e_ += blockDim.x) {
+        const int i = e_ % m, j = e_ / m;
+        a[i * S + j] = (i < c && j < c) ? (float)(A64[i * S + j] * sc) : 0.0f;
+        v[i * S + j] = (i == j) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+
+    // ---- FP32 cyclic Jacobi, round-robin pairing (m/2 disjoint rotations per round) -------
+    const int half = m / 2;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (tid == 0) anyRot = 0;
+        __syncthreads();
+        for (int rnd = 0; rnd < m - 1; ++rnd) {
+            for (int i = tid; i < half; i += blockDim.x) {
+                int p, q;
+                if (i == 0) { p = rnd; q = m - 1; }
+                else { p = (rnd + i) % (m - 1); q = (rnd - i + (m - 1)) % (m - 1); }
+                if (p > q) { int t = p; p = q; q = t; }
+                const float app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
+                float cs = 1.0f, sn = 0.0f;
+                int rot = 0;
+                if (fabsf(apq) > fmaxf(1e-7f * sqrtf(fabsf(app * aqq)), 1e-36f)) {
+                    const float th = (aqq - app) / (2.0f * apq);
+                    float t;
+                    if (fabsf(th) > 1e18f) t = 0.5f / th;
+                    else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
+                    cs = rsqrtf(t * t + 1.0f);
+                    sn = t * cs;
+                    rot = 1;
+                }
+                partner[p] = q; partner[q] = p;
+                coefS[p] = cs; coefP[p] = -sn;
+                coefS[q] = cs; coefP[q] = sn;
+                rotated[i] = rot;
+                if (rot) anyRot = 1;
+            }
+            __syncthreads();
+            for (int e_ = tid; e_ < half * half; e_ += blockDim.x) {
+                const int pi = e_ % half, pj = e_ / half;
+                if (!rotated[pi] && !rotated[pj]) continue;
+                int p1, q1, p2, q2;
+                if (pi == 0) { p1 = rnd; q1 = m - 1; } else { p1 = (rnd + pi) % (m - 1); q1 = (rnd - pi + (m - 1)) % (m - 1); }
+                if (pj == 0) { p2 = rnd; q2 = m - 1; } else { p2 = (rnd + pj) % (m - 1); q2 = (rnd - pj + (m - 1)) % (m - 1); }
+                const int xs[2] = {p1, q1}, ys[2] = {p2, q2};
+                float o[2][2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const int x = xs[u], y = ys[w];
+                        const int xp = partner[x], yp = partner[y];
+                        const float cx = coefS[x], sx = coefP[x], cy = coefS[y], sy = coefP[y];
+                        o[u][w] = cx * (cy * a[x * S + y] + sy * a[x * S + yp]) +
+                                  sx * (cy * a[xp * S + y] + sy * a[xp * S + yp]);
+                    }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) a[xs[u] * S + ys[w]] = o[u][w];
+                if (pi == pj && rotated[pi]) {
+                    a[xs[0] * S + xs[1]] = 0.0f;
+                    a[xs[1] * S + xs[0]] = 0.0f;
+                }
+            }
+            for (int e_ = tid; e_ < m * half; e_ += blockDim.x) {
+                const int r = e_ % m, pi = e_ / m;
+                if (!rotated[pi]) continue;
+                int p, q;
+                if (pi == 0) { p = rnd; q = m - 1; } else { p = (rnd + pi) % (m - 1); q = (rnd - pi + (m - 1)) % (m - 1); }
+                const float vp = v[r * S + p], vq = v[r * S + q];
+                v[r * S + p] = coefS[p] * vp + coefP[p] * vq;
+                v[r * S + q] = coefS[q] * vq + coefP[q] * vp;
+            }
+            __syncthreads();
+        }
+        if (!anyRot) break;
+        __syncthreads();
+    }
+
+    // ---- ascending order of the FP32 eigenvalues (ties by index) -------------------------
+    for (int i = tid; i < c; i += blockDim.x) {
+        const float di = a[i * S + i];
+        int rk = 0;
+        for (int j = 0; j < c; ++j) {
+            const float dj = a[j * S + j];
+            rk += (dj < di) || (dj == di && j < i);
+        }
+        order[rk] = i;
+    }
+    __syncthreads();
+    for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
+        const int r = e_ % c, j = e_ / c;                // V64[:, j] = v[:, order[j]]
+        V64[r * S + j] = (double)v[r * S + order[j]];
+    }
+    __syncthreads();
+
+    // ---- FP64 Cholesky-QR of V64 (columns in ascending order): V64 <- V64 L^-T ------------
+    for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
+        const int i = e_ % c, j = e_ / c;
+        if (i < j) continue;
+        double s_ = 0.0;
+        for (int r = 0; r < c; ++r) s_ = fma(V64[r * S + i], V64[r * S + j], s_);
+        G[i * S + j] = s_;                               // lower triangle of V^T V
+    }
+    __syncthreads();
+    for (int k = 0; k < c; ++k) {
+        if (tid == 0) G[k * S + k] = sqrt(fmax(G[k * S + k], 1e-300));
+        __syncthreads();
+        const double lkk = G[k * S + k];
+        for (int i = k + 1 + tid; i < c; i += blockDim.x) G[i * S + k] /= lkk;
+        __syncthreads();
+        for (int e_ = tid; e_ < (c - k - 1) * (c - k - 1); e_ += blockDim.x) {
+            const int i = k + 1 + e_ % (c - k - 1), j = k + 1 + e_ / (c - k - 1);
+            if (j <= i) G[i * S + j] -= G[i * S + k] * G[j * S + k];
+        }
+        __syncthreads();
+    }
+    for (int r = tid; r < c; r += blockDim.x) {            // row r: solve L y = V64[r, :]^T
+        for (int j = 0; j < c; ++j) {
+            double s_ = V64[r * S + j];
+            for (int i = 0; i < j; ++i) s_ = fma(-G[j * S + i], V64[r * S + i], s_);
+            V64[r * S + j] = s_ / G[j * S + j];
+        }
+    }
+    __syncthreads();
+
+    // ---- eigenvalues and outputs (descending) --------------------------------------------
+    for (int j = tid; j < c; j += blockDim.x) {
+        double lam;
+        if (rq) {
+            lam = 0.0;
+            for (int i = 0; i < c; ++i) {
+                double t = 0.0;
+                for (int k2 = 0; k2 < c; ++k2) t = fma(A64[i * S + k2], V64[k2 * S + j], t);
+                lam = fma(V64[i * S + j], t, lam);
+            }
+        } else {
+            lam = dmax * (double)a[order[j] * S + order[j]];
+        }
+        evb[c - 1 - j] = lam;
+    }
+    for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
+        const int r = e_ % c, j = e_ / c;
+        Vb[r + (long long)(c - 1 - j) * ldv] = V64[r * S + j];
+    }
+}
+
+size_t gjacobi_smem() {
+    const int S = kMaxC + 1;
+    return sizeof(double) * 3 * (size_t)kMaxC * S + sizeof(float) * (2 * (size_t)kMaxC * S + 2 * kMaxC) +
+           sizeof(int) * 3 * kMaxC;
+}
+
+void launch_gjacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
+                    const int* dims, int dstride, int cmax, double* ev, long long bsE,
+                    double* V, int ldv, long long bsV, bool rq)
+{
+    if (batch <= 0) return;
+    const bool prof = prof_active(KC_JACOBI);
+    ProfMark mark;
+    if (prof) prof_begin(st, mark);
+    note_launch(); gjacobi_kernel<<<batch, kEigThreads, gjacobi_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, rq ? 1 : 0, prof ? 1 : 0);
+    if (prof) prof_end(st, mark);
+}
+
 size_t symeig_smem() {
     const int S = kMaxC + 1;
     return sizeof(double) * (2 * (size_t)kMaxC * S + 7 * kMaxC + kGrid) + sizeof(int) * kGrid;
@@ -352,8 +588,11 @@ void launch_symeig(cudaStream_t st, int batch, const double* A, int lda, long lo
 
 cudaError_t set_symeig_attributes()
 {
-    return cudaFuncSetAttribute(symeig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)symeig_smem());
+    cudaError_t e = cudaFuncSetAttribute(symeig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)symeig_smem());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(gjacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gjacobi_smem());
 }
 
 }  // namespace fc

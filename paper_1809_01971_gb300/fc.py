@@ -105,7 +105,7 @@ def lib() -> C.CDLL:
             "fc_launch_count": (C.c_ulonglong, []),
             "fc_inner_static": (I, [cp_p, cp_p, V, V]),
             "fc_prof_enable": (I, [I]),
-            "fc_symeig": (I, [I, I, V, I, C.c_longlong, V, C.c_longlong, V, I, C.c_longlong, V]),
+            "fc_symeig": (I, [I, I, I, V, I, C.c_longlong, V, C.c_longlong, V, I, C.c_longlong, V]),
             "fc_prof_read": (I, [C.POINTER(C.c_longlong), C.POINTER(D), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
@@ -329,16 +329,17 @@ def fc_inner_static(x: CP, y: CP, out: torch.Tensor, stream=None) -> torch.Tenso
     return out
 
 
-def fc_symeig(A: torch.Tensor, stream=None):
+def fc_symeig(A: torch.Tensor, method: int = 0, stream=None):
     """Eigen-decomposition of a batch (b, m, m) of symmetric FP64 CUDA matrices:
-    (w descending (b, m), V (b, m, m) with eigenvectors as columns)."""
+    (w descending (b, m), V (b, m, m) with eigenvectors as columns).  method 0: Householder /
+    bisection / inverse iteration; method 1: the truncation's graded Jacobi solver."""
     if A.dim() == 2:
         A = A.unsqueeze(0)
     A = A.contiguous()
     bsz, m, _ = A.shape
     w = torch.empty(bsz, m, dtype=torch.float64, device=A.device)
     Vt = torch.empty(bsz, m, m, dtype=torch.float64, device=A.device)   # column-major V = Vt^T
-    _check("fc_symeig", lib().fc_symeig(bsz, m, C.c_void_p(A.data_ptr()), m, m * m,
+    _check("fc_symeig", lib().fc_symeig(int(method), bsz, m, C.c_void_p(A.data_ptr()), m, m * m,
                                         C.c_void_p(w.data_ptr()), m, C.c_void_p(Vt.data_ptr()), m,
                                         m * m, _stream(stream)))
     return w, Vt.transpose(1, 2)
