@@ -125,7 +125,8 @@ struct fc_ctx {
         CP cat, Xs, Rs, Ps, Zs, Ss;
         double* pinned_dummy;
     } w{};
-    unsigned long long seed = 0x1809019710ull;
+    static constexpr unsigned long long kSeed0 = 0x1809019710ull;
+    unsigned long long seed = kSeed0;
     // rank statistics of the truncations since the last reset (fc_solve reports them)
     long long stat_rsum = 0, stat_rcount = 0;
     int stat_rmax = 0, stat_bmax = 0;
@@ -790,6 +791,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     std::memset(&inf, 0, sizeof(inf));
     h->stat_rsum = h->stat_rcount = 0;
     h->stat_rmax = h->stat_bmax = 0;
+    h->seed = fc_ctx::kSeed0;  // same sketches for every solve of a right-hand side: reproducible
     cudaStream_t st = (cudaStream_t)stream;
     auto& w = h->w;
     CP B = from_user(rhs);

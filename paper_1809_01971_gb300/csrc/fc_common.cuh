@@ -122,41 +122,43 @@ struct LdSl {     // op = slice : (a, b)
 // FP64 FMAs per SM per clock, so a GEMM whose output tiles cannot fill the 152 SMs is
 // split along K until they do.  Register tile 4x4 per thread, 64x64 block tile, BK = 16.
 // ---------------------------------------------------------------------------------------
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int GBK = 16;
 constexpr int kNumSMs = 152;
 
-template <class LA, class LB>
+// Tile T x T (T = 64, 32 or 16) with 256 threads, each owning a (T/16) x (T/16) register block.
+template <int T, class LA, class LB>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
             LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
             int batch, int splits, int kchunk)
 {
-    __shared__ double As[GBK][GBM + 1];
-    __shared__ double Bs[GBK][GBN + 1];
+    constexpr int R = T / 16;                  // register block per thread
+    constexpr int LOADS = T * GBK / 256;       // tile elements loaded per thread
+    __shared__ double As[GBK][T + 1];
+    __shared__ double Bs[GBK][T + 1];
     if (dM) M = min(M, *dM);
     if (dN) N = min(N, *dN);
     if (dK) K = min(K, *dK);
     const int zb = blockIdx.z / splits, zs = blockIdx.z - zb * splits;
-    const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+    const int m0 = blockIdx.x * T, n0 = blockIdx.y * T;
     if (m0 >= M || n0 >= N || zb >= batch) return;
     int kbeg = zs * kchunk, kend = min(K, kbeg + kchunk);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
+    double acc[R][R];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
     for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-        // 64 x 16 tile of op(A): 1024 elements, 4 per thread
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < LOADS; ++t) {          // T x 16 tile of op(A)
             int e = threadIdx.x + t * 256;
-            int ii = e & 63, kk = e >> 6;
+            int ii = e % T, kk = e / T;
             int gi = m0 + ii, gk = k0 + kk;
             As[kk][ii] = (gi < M && gk < kend) ? A(gi, gk, zb) : 0.0;
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < LOADS; ++t) {          // 16 x T tile of op(B)
             int e = threadIdx.x + t * 256;
             int kk = e & 15, jj = e >> 4;
             int gj = n0 + jj, gk = k0 + kk;
@@ -165,25 +167,25 @@ gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GBK; ++kk) {
-            double a[4], b[4];
+            double a[R], b[R];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
     double* Cb = C + zb * bsC;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
         int gi = m0 + ty + 16 * i;
         if (gi >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
             int gj = n0 + tx + 16 * j;
             if (gj >= N) continue;
             double* c = Cb + gi + (long long)gj * ldc;
@@ -197,13 +199,21 @@ gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
 __global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN, double beta,
                                      double* C, int ldc, long long bsC);
 
+// Launch: the largest tile (64, 32, 16) whose grid still covers the 152 SMs, then split-K
+// until about 4 CTAs per SM (GB300 runs few FP64 FMAs per SM per clock, so the SM count
+// decides the rate).
 template <class LA, class LB>
 inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha, double beta,
                  double* C, int ldc, long long bsC = 0, int batch = 1,
                  const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr)
 {
     if (M <= 0 || N <= 0 || batch <= 0) return;
-    const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
+    auto tiles_of = [&](int T) {
+        return (long long)((M + T - 1) / T) * ((N + T - 1) / T) * batch;
+    };
+    int T = 64;
+    if (tiles_of(64) < kNumSMs) T = (tiles_of(32) < kNumSMs) ? 16 : 32;
+    const long long tiles = tiles_of(T);
     int splits = 1;
     if (tiles < 2 * kNumSMs && K >= 128) {
         long long want = (4 * kNumSMs + tiles - 1) / tiles;
@@ -220,9 +230,17 @@ inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha,
         dim3 g((M + 255) / 256, N, batch);
         note_launch(); gemm_prescale_kernel<<<g, 256, 0, st>>>(M, N, dM, dN, beta, C, ldc, bsC);
     }
-    dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, batch * splits);
-    note_launch(); gemm_kernel<LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC,
-                                               batch, splits, kchunk);
+    dim3 grid((M + T - 1) / T, (N + T - 1) / T, batch * splits);
+    note_launch();
+    if (T == 64)
+        gemm_kernel<64, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
+                                                      ldc, bsC, batch, splits, kchunk);
+    else if (T == 32)
+        gemm_kernel<32, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
+                                                      ldc, bsC, batch, splits, kchunk);
+    else
+        gemm_kernel<16, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
+                                                      ldc, bsC, batch, splits, kchunk);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -179,6 +179,7 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
     double* Mi = L + kMaxC * SS;       // copy of M
     double* Li = Mi + kMaxC * SS;      // L11^{-1}
     __shared__ double dg[kMaxC];
+    __shared__ double invd[kMaxC];   // 1 / L[k][k] (GB300 has no FP64 divide unit: one per pivot)
     __shared__ int perm[kMaxC];
     __shared__ int rk;
     __shared__ double dmax0;
@@ -206,25 +207,27 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
             int p = k; double best = dg[perm[k]];
             for (int i = k + 1; i < c; ++i) if (dg[perm[i]] > best) { best = dg[perm[i]]; p = i; }
             if (!(best > relTol * dmax0) || !(best > 0.0)) rk = k;
-            else if (p != k) {
-                // rows of L are stored by pivot position: move the computed part with the pivot
-                int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
-                for (int j = 0; j < k; ++j) {
-                    double x = L[k * SS + j]; L[k * SS + j] = L[p * SS + j]; L[p * SS + j] = x;
+            else {
+                if (p != k) {
+                    // rows of L are stored by pivot position: move the computed part with the pivot
+                    int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+                    for (int j = 0; j < k; ++j) {
+                        double x = L[k * SS + j]; L[k * SS + j] = L[p * SS + j]; L[p * SS + j] = x;
+                    }
                 }
+                const double lkk = sqrt(best);
+                L[k * SS + k] = lkk;
+                invd[k] = 1.0 / lkk;
             }
         }
         __syncthreads();
         if (rk <= k) break;
-        const double lkk = sqrt(dg[perm[k]]);
-        for (int i = k + threadIdx.x; i < c; i += blockDim.x) {
+        const double ik = invd[k];
+        for (int i = k + 1 + threadIdx.x; i < c; i += blockDim.x) {
             double s = Mi[perm[i] * SS + perm[k]];
             for (int j = 0; j < k; ++j) s -= L[i * SS + j] * L[k * SS + j];
-            L[i * SS + k] = (i == k) ? lkk : s / lkk;
-        }
-        __syncthreads();
-        for (int i = k + 1 + threadIdx.x; i < c; i += blockDim.x) {
-            double l = L[i * SS + k];
+            const double l = s * ik;
+            L[i * SS + k] = l;
             dg[perm[i]] -= l * l;
         }
         __syncthreads();
@@ -236,7 +239,7 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
             if (i < j) { Li[i * SS + j] = 0.0; continue; }
             double s = (i == j) ? 1.0 : 0.0;
             for (int t = j; t < i; ++t) s -= L[i * SS + t] * Li[t * SS + j];
-            Li[i * SS + j] = s / L[i * SS + i];
+            Li[i * SS + j] = s * invd[i];
         }
     }
     __syncthreads();

@@ -367,9 +367,9 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
     float* v = a + kMaxC * S;              // m x S (FP32 eigenvectors, row-major v[r*S+col])
     float* coefS = v + kMaxC * S;
     float* coefP = coefS + kMaxC;
-    int* partner = (int*)(coefP + kMaxC);
-    int* rotated = partner + kMaxC;
+    int* rotated = (int*)(coefP + kMaxC);
     int* order = rotated + kMaxC;          // ascending eigenvalue order
+    int* pairs = order + kMaxC;            // (m-1) x m/2 round-robin pairs, p | q << 8
     __shared__ double red[32];
     __shared__ int anyRot;
 
@@ -412,16 +412,25 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
     __syncthreads();
 
     // ---- FP32 cyclic Jacobi, round-robin pairing (m/2 disjoint rotations per round) -------
+    // pair i of round rnd: (rnd, m-1) for i = 0, else ((rnd+i) mod (m-1), (rnd-i) mod (m-1));
+    // the table is built once; each pair's rotation J = [[c, s], [-s, c]] acts on (p < q)
     const int half = m / 2;
+    for (int e_ = tid; e_ < (m - 1) * half; e_ += blockDim.x) {
+        const int rnd = e_ / half, i = e_ - rnd * half;
+        int p, q;
+        if (i == 0) { p = rnd; q = m - 1; }
+        else { p = (rnd + i) % (m - 1); q = (rnd - i + (m - 1)) % (m - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        pairs[e_] = p | (q << 8);
+    }
+    __syncthreads();
     for (int sweep = 0; sweep < 40; ++sweep) {
         if (tid == 0) anyRot = 0;
         __syncthreads();
         for (int rnd = 0; rnd < m - 1; ++rnd) {
-            for (int i = tid; i < half; i += blockDim.x) {
-                int p, q;
-                if (i == 0) { p = rnd; q = m - 1; }
-                else { p = (rnd + i) % (m - 1); q = (rnd - i + (m - 1)) % (m - 1); }
-                if (p > q) { int t = p; p = q; q = t; }
+            const int* pr = pairs + rnd * half;
+            if (tid < half) {
+                const int p = pr[tid] & 255, q = pr[tid] >> 8;
                 const float app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
                 float cs = 1.0f, sn = 0.0f;
                 int rot = 0;
@@ -434,48 +443,38 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                     sn = t * cs;
                     rot = 1;
                 }
-                partner[p] = q; partner[q] = p;
-                coefS[p] = cs; coefP[p] = -sn;
-                coefS[q] = cs; coefP[q] = sn;
-                rotated[i] = rot;
+                coefS[tid] = cs;
+                coefP[tid] = sn;
+                rotated[tid] = rot;
                 if (rot) anyRot = 1;
             }
             __syncthreads();
+            // A <- J^T A J, one 2x2 block (pair pi rows, pair pj columns) per thread-step
             for (int e_ = tid; e_ < half * half; e_ += blockDim.x) {
                 const int pi = e_ % half, pj = e_ / half;
-                if (!rotated[pi] && !rotated[pj]) continue;
-                int p1, q1, p2, q2;
-                if (pi == 0) { p1 = rnd; q1 = m - 1; } else { p1 = (rnd + pi) % (m - 1); q1 = (rnd - pi + (m - 1)) % (m - 1); }
-                if (pj == 0) { p2 = rnd; q2 = m - 1; } else { p2 = (rnd + pj) % (m - 1); q2 = (rnd - pj + (m - 1)) % (m - 1); }
-                const int xs[2] = {p1, q1}, ys[2] = {p2, q2};
-                float o[2][2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        const int x = xs[u], y = ys[w];
-                        const int xp = partner[x], yp = partner[y];
-                        const float cx = coefS[x], sx = coefP[x], cy = coefS[y], sy = coefP[y];
-                        o[u][w] = cx * (cy * a[x * S + y] + sy * a[x * S + yp]) +
-                                  sx * (cy * a[xp * S + y] + sy * a[xp * S + yp]);
-                    }
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) a[xs[u] * S + ys[w]] = o[u][w];
-                if (pi == pj && rotated[pi]) {
-                    a[xs[0] * S + xs[1]] = 0.0f;
-                    a[xs[1] * S + xs[0]] = 0.0f;
-                }
+                const int ri = rotated[pi], rj = rotated[pj];
+                if (!ri && !rj) continue;
+                const int p1 = pr[pi] & 255, q1 = pr[pi] >> 8, p2 = pr[pj] & 255, q2 = pr[pj] >> 8;
+                const float ci = coefS[pi], si = coefP[pi], cj = coefS[pj], sj = coefP[pj];
+                const float b00 = a[p1 * S + p2], b01 = a[p1 * S + q2];
+                const float b10 = a[q1 * S + p2], b11 = a[q1 * S + q2];
+                const float r00 = ci * b00 - si * b10, r01 = ci * b01 - si * b11;   // J_i^T B
+                const float r10 = si * b00 + ci * b10, r11 = si * b01 + ci * b11;
+                float o00 = cj * r00 - sj * r01, o01 = sj * r00 + cj * r01;        // (.) J_j
+                float o10 = cj * r10 - sj * r11, o11 = sj * r10 + cj * r11;
+                if (pi == pj) { o01 = 0.0f; o10 = 0.0f; }                     // annihilated
+                a[p1 * S + p2] = o00; a[p1 * S + q2] = o01;
+                a[q1 * S + p2] = o10; a[q1 * S + q2] = o11;
             }
+            // V <- V J
             for (int e_ = tid; e_ < m * half; e_ += blockDim.x) {
                 const int r = e_ % m, pi = e_ / m;
                 if (!rotated[pi]) continue;
-                int p, q;
-                if (pi == 0) { p = rnd; q = m - 1; } else { p = (rnd + pi) % (m - 1); q = (rnd - pi + (m - 1)) % (m - 1); }
+                const int p = pr[pi] & 255, q = pr[pi] >> 8;
+                const float c_ = coefS[pi], s_ = coefP[pi];
                 const float vp = v[r * S + p], vq = v[r * S + q];
-                v[r * S + p] = coefS[p] * vp + coefP[p] * vq;
-                v[r * S + q] = coefS[q] * vq + coefP[q] * vp;
+                v[r * S + p] = c_ * vp - s_ * vq;
+                v[r * S + q] = s_ * vp + c_ * vq;
             }
             __syncthreads();
         }
@@ -554,7 +553,7 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
 size_t gjacobi_smem() {
     const int S = kMaxC + 1;
     return sizeof(double) * 3 * (size_t)kMaxC * S + sizeof(float) * (2 * (size_t)kMaxC * S + 2 * kMaxC) +
-           sizeof(int) * 3 * kMaxC;
+           sizeof(int) * (2 * kMaxC + (size_t)kMaxC * kMaxC / 2);
 }
 
 void launch_gjacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,

@@ -34,7 +34,11 @@ def test_symeig_matches_lapack(m, method):
     w, V = fc.fc_symeig(A, method=method)
     torch.cuda.synchronize()
     w, V = w.cpu().numpy(), V.cpu().numpy()
-    tol_w = 1e-13 if method == 0 else 1e-9
+    # method 0: FP64 accuracy.  method 1 resolves eigen-directions to FP32 precision relative
+    # to the grading of the matrix (what the truncation needs; see the graded-rank test below)
+    # and returns FP64 Rayleigh quotients: eigenvalues within ~(1e-7)^2 ... 1e-7 relative to
+    # ||A|| depending on the gaps, eigenvectors orthonormal to FP64 precision.
+    tol_w = 1e-13 if method == 0 else 1e-7
     for b, (name, M) in enumerate(zip(names, mats)):
         wn = np.linalg.eigvalsh(M)[::-1]
         nA = max(np.linalg.norm(M, 2), 1e-300)
@@ -44,8 +48,9 @@ def test_symeig_matches_lapack(m, method):
         print(f"method {method} m={m} {name}: eig {e_w:.1e} orth {e_o:.1e} resid {e_r:.1e}")
         assert e_w <= tol_w
         assert e_o <= 1e-12
-        if method == 0 and name != "zero":
-            assert e_r <= 1e-12
+        if name != "zero":
+            assert e_r <= (1e-12 if method == 0 else 1e-5)
+        if method == 0:
             assert np.all(np.diff(w[b]) <= 0)
 
 
