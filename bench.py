@@ -171,9 +171,9 @@ def run_reference(args):
 # FP64 peak of the chip from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
 # x 2 flop x 2.07 GHz (an FP64 probe on this part measured 1.19 TFLOP/s at 1.9-2.07 GHz).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# Jacobi kernel DRAM traffic per launch (dram__bytes_read.sum + write) from one ncu capture of
-# this kernel (3-matrix launch of the n=255 solve); None once the kernel changes.
-JACOBI_TRAFFIC_BYTES = 89856
+# Eigen-solver DRAM traffic per launch (dram__bytes_read.sum + write) from one ncu capture of
+# the current kernel (3-matrix launch of the n=255 solve); None when not captured for it.
+EIG_TRAFFIC_BYTES = None
 
 
 def main():
@@ -320,9 +320,10 @@ def main():
     if jac_n > 0 and jac_ms > 0:
         achieved = jac_work / jac_n / (jac_ms / jac_n * 1e-3) / 1e12     # TFLOP/s
         peak = FP64_PEAK_GFLOPS / 1e3
-        roofline = {"kernel": "jacobi_eig_kernel (FP64 symmetric eigen-solves of the RHOSVD)",
+        roofline = {"kernel": "gjacobi_kernel (graded eigen-solves of the RHOSVD: FP32 Jacobi "
+                              "sweeps, FP64 orthonormalisation)",
                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": JACOBI_TRAFFIC_BYTES,
+                    "frac": achieved / peak, "traffic": EIG_TRAFFIC_BYTES,
                     "peak_kind": "FP64, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                     "work": "9 c^3 flop per c x c matrix (textbook dense eigen-solve count)",
                     "launches": jac_n, "avg_launch_us": 1e3 * jac_ms / jac_n,

@@ -167,92 +167,98 @@ void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long lo
 // Diagonal pivoting stops when the largest remaining diagonal is <= relTol * max diag(M);
 // with rank r and pivot order piv, Y P[:, :r] = Q R11, and T[:, :r] = P[:, :r] R11^{-1}
 // (T zero elsewhere) gives Q = Y T with orthonormal first r columns.  rank[b*rstride] = r.
+// One warp per matrix: the factorisation is a chain of c dependent pivot steps, so warp
+// shuffles (pivot arg-max) and __syncwarp replace block barriers; each lane owns rows
+// (and later columns of L^-1) lane and lane + 32.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32)
 pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* dims, int dstride,
              int cmax, double relTol, double* __restrict__ T, int ldt, long long bsT,
              int* rank, int rstride)
 {
     extern __shared__ double sm[];
     constexpr int SS = kMaxC + 1;
-    double* L = sm;                    // L[i*SS + k], i in permuted order
+    double* L = sm;                    // L[i*SS + k], i in pivot-position order
     double* Mi = L + kMaxC * SS;       // copy of M
     double* Li = Mi + kMaxC * SS;      // L11^{-1}
     __shared__ double dg[kMaxC];
-    __shared__ double invd[kMaxC];   // 1 / L[k][k] (GB300 has no FP64 divide unit: one per pivot)
+    __shared__ double invd[kMaxC];     // 1 / L[k][k] (one reciprocal per pivot)
     __shared__ int perm[kMaxC];
-    __shared__ int rk;
-    __shared__ double dmax0;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
     const int b = blockIdx.x;
     int c = cmax;
     if (dims) c = min(dims[b * dstride], cmax);
     if (c < 0) c = 0;
     const double* Mb = M + b * bsM;
-    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
-        int i = e % c, j = e / c;
+    for (int e = lane; e < c * c; e += 32) {
+        const int i = e % c, j = e / c;
         Mi[i * SS + j] = Mb[i + (long long)j * ldm];
     }
-    for (int i = threadIdx.x; i < kMaxC; i += blockDim.x) perm[i] = i;
-    __syncthreads();
-    for (int i = threadIdx.x; i < c; i += blockDim.x) dg[i] = Mi[i * SS + i];
-    if (threadIdx.x == 0) {
-        double mx = 0.0;
-        for (int i = 0; i < c; ++i) mx = fmax(mx, Mi[i * SS + i]);
-        dmax0 = mx;
-        rk = c;
-    }
-    __syncthreads();
+    for (int i = lane; i < kMaxC; i += 32) perm[i] = i;
+    __syncwarp();
+    double mx = 0.0;
+    for (int i = lane; i < c; i += 32) { dg[i] = Mi[i * SS + i]; mx = fmax(mx, dg[i]); }
+    const double dmax0 = warp_max(mx);
+    __syncwarp();
+    int rk = c;
     for (int k = 0; k < c; ++k) {
-        if (threadIdx.x == 0) {
-            int p = k; double best = dg[perm[k]];
-            for (int i = k + 1; i < c; ++i) if (dg[perm[i]] > best) { best = dg[perm[i]]; p = i; }
-            if (!(best > relTol * dmax0) || !(best > 0.0)) rk = k;
-            else {
-                if (p != k) {
-                    // rows of L are stored by pivot position: move the computed part with the pivot
-                    int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
-                    for (int j = 0; j < k; ++j) {
-                        double x = L[k * SS + j]; L[k * SS + j] = L[p * SS + j]; L[p * SS + j] = x;
-                    }
-                }
-                const double lkk = sqrt(best);
-                L[k * SS + k] = lkk;
-                invd[k] = 1.0 / lkk;
-            }
+        // pivot: largest remaining diagonal among positions k..c-1 (ties: smallest position)
+        double best = -1.0;
+        int bp = c;
+        for (int p = k + lane; p < c; p += 32) {
+            const double v = dg[perm[p]];
+            if (v > best || (v == best && p < bp)) { best = v; bp = p; }
         }
-        __syncthreads();
-        if (rk <= k) break;
-        const double ik = invd[k];
-        for (int i = k + 1 + threadIdx.x; i < c; i += blockDim.x) {
-            double s = Mi[perm[i] * SS + perm[k]];
-            for (int j = 0; j < k; ++j) s -= L[i * SS + j] * L[k * SS + j];
-            const double l = s * ik;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(full, best, o);
+            const int op = __shfl_xor_sync(full, bp, o);
+            if (ob > best || (ob == best && op < bp)) { best = ob; bp = op; }
+        }
+        if (!(best > relTol * dmax0) || !(best > 0.0)) { rk = k; break; }   // uniform
+        if (bp != k) {
+            // rows of L are stored by pivot position: move the computed part with the pivot
+            if (lane == 0) { const int t = perm[k]; perm[k] = perm[bp]; perm[bp] = t; }
+            for (int j = lane; j < k; j += 32) {
+                const double x = L[k * SS + j]; L[k * SS + j] = L[bp * SS + j]; L[bp * SS + j] = x;
+            }
+            __syncwarp();
+        }
+        const double lkk = sqrt(best);
+        const double ik = 1.0 / lkk;
+        if (lane == 0) { L[k * SS + k] = lkk; invd[k] = ik; }
+        const int pk = perm[k];
+        for (int i = k + 1 + lane; i < c; i += 32) {
+            double s0 = Mi[perm[i] * SS + pk];
+            for (int j = 0; j < k; ++j) s0 = fma(-L[i * SS + j], L[k * SS + j], s0);
+            const double l = s0 * ik;
             L[i * SS + k] = l;
             dg[perm[i]] -= l * l;
         }
-        __syncthreads();
+        __syncwarp();
     }
     const int r = rk;
-    // L11^{-1} (lower triangular), column j by thread j: forward substitution L11 x = e_j
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        for (int i = 0; i < r; ++i) {
-            if (i < j) { Li[i * SS + j] = 0.0; continue; }
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int t = j; t < i; ++t) s -= L[i * SS + t] * Li[t * SS + j];
-            Li[i * SS + j] = s * invd[i];
+    // L11^{-1} (lower triangular): column j by lane j (and j + 32), forward substitution
+    for (int j = lane; j < r; j += 32) {
+        for (int i = 0; i < j; ++i) Li[i * SS + j] = 0.0;
+        Li[j * SS + j] = invd[j];
+        for (int i = j + 1; i < r; ++i) {
+            double s0 = 0.0;
+            for (int t = j; t < i; ++t) s0 = fma(-L[i * SS + t], Li[t * SS + j], s0);
+            Li[i * SS + j] = s0 * invd[i];
         }
     }
-    __syncthreads();
+    __syncwarp();
     // R11^{-1} = (L11^T)^{-1} = (L11^{-1})^T ; T[perm[j], i] = Rinv[j, i] = Linv[i, j]
     double* Tb = T + b * bsT;
-    for (int e = threadIdx.x; e < cmax * cmax; e += blockDim.x)
-        Tb[(e % cmax) + (long long)(e / cmax) * ldt] = 0.0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        int j = e % r, i = e / r;
+    for (int e = lane; e < cmax * cmax; e += 32) Tb[(e % cmax) + (long long)(e / cmax) * ldt] = 0.0;
+    __syncwarp();
+    for (int e = lane; e < r * r; e += 32) {
+        const int j = e % r, i = e / r;
         if (j <= i) Tb[perm[j] + (long long)i * ldt] = Li[i * SS + j];
     }
-    if (threadIdx.x == 0) rank[b * rstride] = r;
+    if (lane == 0) rank[b * rstride] = r;
 }
 
 size_t pchol_smem() { return sizeof(double) * 3 * kMaxC * (kMaxC + 1); }
@@ -273,7 +279,7 @@ void launch_pchol(cudaStream_t st, int batch, const double* M, int ldm, long lon
 {
     if (batch <= 0) return;
     const size_t sm = pchol_smem();
-    note_launch(); pchol_kernel<<<batch, 256, sm, st>>>(M, ldm, bsM, dims, dstride, cmax, relTol, T, ldt, bsT,
+    note_launch(); pchol_kernel<<<batch, 32, sm, st>>>(M, ldm, bsM, dims, dstride, cmax, relTol, T, ldt, bsT,
                                          rank, rstride);
 }
 

@@ -424,7 +424,7 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         pairs[e_] = p | (q << 8);
     }
     __syncthreads();
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int sweep = 0; sweep < 15; ++sweep) {
         if (tid == 0) anyRot = 0;
         __syncthreads();
         for (int rnd = 0; rnd < m - 1; ++rnd) {
@@ -434,7 +434,9 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                 const float app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
                 float cs = 1.0f, sn = 0.0f;
                 int rot = 0;
-                if (fabsf(apq) > fmaxf(1e-7f * sqrtf(fabsf(app * aqq)), 1e-36f)) {
+                // relative threshold a few FP32 ulps above rounding noise; at most 15
+                // sweeps (quadratic convergence: ~5 suffice for an ordering basis)
+                if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), 1e-36f)) {
                     const float th = (aqq - app) / (2.0f * apq);
                     float t;
                     if (fabsf(th) > 1e18f) t = 0.5f / th;
