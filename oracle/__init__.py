@@ -25,8 +25,10 @@ Modules
   truncate    RHOSVD canonical -> Tucker -> canonical rank truncation
               (Section 5, eqn:two_level) and the 2D reduced SVD.
   pcg         Algorithm 1 (low-rank PCG).
-  full        full-format eigenbasis solve (eqn:DiagFLaplace3D) and a dense
-              eigendecomposition brute force of A^{+-alpha} for small n.
+  full        full-format eigenbasis solve (eqn:DiagFLaplace3D), the state
+              y = beta A^-alpha u (eqn:State), the directionally fractional
+              Laplacian solve (Remark after Lemma 4.1), and dense
+              eigendecomposition brute forces of both for small n.
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, brute force or library routines; none is "parity unpinned".

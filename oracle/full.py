@@ -37,6 +37,37 @@ def apply_full(x: np.ndarray, alpha, beta, gamma_) -> np.ndarray:
     return apply_g_full(x, lambda r: g_control(r, alpha, beta, gamma_))
 
 
+def state_full(u: np.ndarray, alpha, beta) -> np.ndarray:
+    """State y = beta A^-alpha u (eqn:State, eqn:L_alp_state) in full format."""
+    return apply_g_full(u, lambda r: beta * r ** (-alpha))
+
+
+def solve_full_directional(b: np.ndarray, alpha, beta, gamma_) -> np.ndarray:
+    """Exact solution of (beta^2 A_(alpha)^-1 + gamma A_(alpha)) u = b for the directionally
+    fractional Laplacian A_(alpha) = sum_l (-Delta_l)^alpha (Remark after Lemma 4.1,
+    eq:Laplace_1Dfract, eq:3b1d): in the DST-I eigenbasis A_(alpha) is diagonal with
+    mu(i) = sum_l lambda_{i_l}^alpha."""
+    mu = rho_full([eigenvalues(m) ** alpha for m in b.shape])
+    return dst_all(dst_all(b) / (beta**2 / mu + gamma_ * mu))
+
+
+def dense_directional(ns, alpha) -> np.ndarray:
+    """Dense A_(alpha) = sum_l I x (A_(l))^alpha x I, (A_(l))^alpha by the 1D eigendecomposition
+    (no DST involved)."""
+    d = len(ns)
+    N = int(np.prod(ns))
+    A = np.zeros((N, N))
+    for l in range(d):
+        w, V = np.linalg.eigh(laplacian_1d(ns[l]))
+        mats = [np.eye(m) for m in ns]
+        mats[l] = V @ np.diag(w**alpha) @ V.T
+        K = mats[0]
+        for M in mats[1:]:
+            K = np.kron(K, M)
+        A += K
+    return A
+
+
 def dense_laplacian(ns) -> np.ndarray:
     """A = sum_l I x ... x A_(l) x ... x I with axis 0 = mode 1 fastest-varying
     last in numpy C order (A acts on x.reshape(-1) of an array of shape ns)."""

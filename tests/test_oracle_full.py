@@ -62,3 +62,32 @@ def test_apply_then_solve_is_identity():
     b = rng.standard_normal((9, 10, 11))
     u = full.solve_full(b, 0.3, 1.0, 1e-2)
     assert np.linalg.norm(full.apply_full(u, 0.3, 1.0, 1e-2) - b) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("ns,alpha", [((6, 5), 0.5), ((4, 3, 5), 0.3), ((5, 5, 4), 1.0)])
+def test_directional_solve_matches_dense(ns, alpha):
+    """Directionally fractional Laplacian (Remark after Lemma 4.1): the eigenbasis solve equals
+    a dense solve with sum_l I x A_(l)^alpha x I built from 1D eigendecompositions; at alpha = 1
+    it coincides with the plain Laplacian operator beta^2 A^-1 + gamma A."""
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(ns)
+    beta, gamma_ = 1.3, 2e-2
+    Ad = full.dense_directional(ns, alpha)
+    M = beta**2 * np.linalg.inv(Ad) + gamma_ * Ad
+    ref = np.linalg.solve(M, b.reshape(-1)).reshape(ns)
+    got = full.solve_full_directional(b, alpha, beta, gamma_)
+    assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+    if alpha == 1.0:
+        plain = full.solve_full(b, 1.0, beta, gamma_)
+        assert np.linalg.norm(got - plain) <= 1e-12 * np.linalg.norm(plain)
+
+
+def test_state_is_beta_A_minus_alpha_u():
+    """eqn:State: y = beta A^-alpha u against the dense spectral definition A^-alpha."""
+    ns = (5, 4, 3)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal(ns)
+    alpha, beta = 0.4, 1.7
+    Am = full.brute_force_power(ns, -alpha)
+    ref = beta * (Am @ u.reshape(-1)).reshape(ns)
+    assert np.linalg.norm(full.state_full(u, alpha, beta) - ref) <= 1e-11 * np.linalg.norm(ref)
