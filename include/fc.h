@@ -69,6 +69,9 @@ typedef struct fc_setup_opts {
     int max_rank;       /* largest CP rank of any iterate after truncation [32]              */
     int max_tucker;     /* largest Tucker rank per mode inside the truncation [48]           */
     int max_input_rank; /* largest rank of a right-hand side / fc_apply input [max_rank]     */
+    int directional;    /* != 0: the directionally fractional operator A_(alpha) =           */
+                        /* sum_l (-Delta_l)^alpha (Remark after Lemma 4.1) in place of A^alpha: */
+                        /* the equation (beta^2 A_(alpha)^-1 + gamma A_(alpha)) u = b [0]    */
 } fc_setup_opts;
 
 typedef struct fc_setup_info {
@@ -121,7 +124,8 @@ int fc_workspace_size(fc_handle h, size_t* bytes);
  * handle keeps the pointer; calls on one handle must not overlap in time. */
 int fc_set_workspace(fc_handle h, void* dev_ptr, size_t bytes);
 
-/* Copy the operator symbol (which=0), or the preconditioner symbol (which=1), as a CP tensor
+/* Copy the operator symbol (which=0), the preconditioner symbol (which=1) or the state symbol
+ * beta rho^-alpha (which=2, eqn:State) as a CP tensor
  * in the eigen-index domain: diag(g(Lambda)) ~ sum_k xi_k E_1[:,k] x .. x E_d[:,k] with
  * E_l[i,k] a function of lambda_i (eqn:Func_of_rho).  out->cap must be >= the symbol rank. */
 int fc_get_symbol(fc_handle h, int which, fc_cp* out, void* stream);
@@ -147,12 +151,18 @@ int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int norma
 
 /* y = trunc(F(A) x, eps) as one fused step (the lines S = trunc(fun(P)) and
  * Z = trunc(precond(R)) of Algorithm 1): which = 0 applies the operator symbol, which = 1 the
- * preconditioner.  The R_A * x->rank (or R_P * x->rank) Khatri-Rao columns of the mat-vec are
+ * preconditioner, which = 2 the state operator beta A^-alpha (see fc_state).  The R_A * x->rank (or R_P * x->rank) Khatri-Rao columns of the mat-vec are
  * never formed in HBM: the truncation (same rule as fc_truncate with normalize = 0) reads them
  * implicitly in the eigen-index domain and applies the inverse DST-I only to the r_l Tucker
  * basis columns (F is orthogonal, Section 3.2).  x->rank <= max_input_rank.  Synchronises. */
 int fc_apply_trunc(fc_handle h, int which, const fc_cp* x, double eps, int max_rank, fc_cp* y,
                    void* stream);
+
+/* State recovery (eqn:State, eqn:L_alp_state): y = trunc(beta A^-alpha u, eps), with the
+ * beta^2 rho^-alpha part of the operator symbol divided by beta (R_minus terms); same layout
+ * and truncation rule as fc_apply_trunc.  (The adjoint of the KKT system is p = (gamma/beta) u:
+ * u with its weights scaled.)  For a handle set up with `directional`, A_(alpha)^-1. */
+int fc_state(fc_handle h, const fc_cp* u, double eps, int max_rank, fc_cp* y, void* stream);
 
 /* *out_host = <x, y> = sum_{k,j} xi_k eta_j prod_l <x_lk, y_lj> (inner products of
  * Algorithm 1).  Synchronises. */

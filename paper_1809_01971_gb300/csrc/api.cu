@@ -113,6 +113,10 @@ struct fc_ctx {
     double *lam = nullptr, *sintab = nullptr;
     double *xiA = nullptr, *EA = nullptr, *GEA = nullptr;   // symbol CP and mode Grams
     double *xiP = nullptr, *EP = nullptr, *GEP = nullptr;   // preconditioner CP and Grams
+    // state symbol beta rho^-alpha: the first RS columns of EA with weights xiA / beta
+    double *xiS = nullptr, *GES = nullptr;
+    int RS = 0;
+    double alpha_eff = 0.0;   // exponent of the symbol's spectrum (1 for the directional operator)
     // workspace (caller-owned)
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -412,17 +416,20 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
 }
 
 // Khatri-Rao input from a CP tensor x and a symbol: Yh = F x (DST of the x factors)
-int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, bool precond, KRIn& kr) {
+// which: 0 = operator symbol, 1 = preconditioner, 2 = state symbol beta rho^-alpha
+int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, int which, KRIn& kr) {
     if (x.rank > h->KIN) return FC_ERANK;
     const long long nK = (long long)h->n * h->KIN;
     const double* in[3] = {x.U[0], x.U[1], x.U[2]};
     double* o[3] = {h->w.Yh, h->w.Yh + nK, h->w.Yh + 2 * nK};
     dst_cols(h, st, x.rank, in, x.ld, o, h->n);
-    kr.xa = precond ? h->xiP : h->xiA;
-    kr.E = precond ? h->EP : h->EA;
-    kr.Ra = precond ? h->RP : h->RA;
-    kr.bsE = (long long)h->n * kr.Ra;
-    kr.GE = precond ? h->GEP : h->GEA;
+    if (which == 1) {
+        kr.xa = h->xiP; kr.E = h->EP; kr.Ra = h->RP; kr.bsE = (long long)h->n * h->RP; kr.GE = h->GEP;
+    } else if (which == 2) {
+        kr.xa = h->xiS; kr.E = h->EA; kr.Ra = h->RS; kr.bsE = (long long)h->n * h->RA; kr.GE = h->GES;
+    } else {
+        kr.xa = h->xiA; kr.E = h->EA; kr.Ra = h->RA; kr.bsE = (long long)h->n * h->RA; kr.GE = h->GEA;
+    }
     kr.xb = x.xi;
     kr.Yh = h->w.Yh;
     kr.S = x.rank;
@@ -461,9 +468,9 @@ int combo_trunc(fc_ctx* h, cudaStream_t st, const CP& x, double a, const CP* y, 
     return truncate_impl(h, st, nullptr, &dn, eps, maxq, out);
 }
 
-int kr_trunc(fc_ctx* h, cudaStream_t st, const CP& x, bool precond, double eps, int maxq, CP& out) {
+int kr_trunc(fc_ctx* h, cudaStream_t st, const CP& x, int which, double eps, int maxq, CP& out) {
     KRIn kr;
-    int rc = kr_from(h, st, x, precond, kr);
+    int rc = kr_from(h, st, x, which, kr);
     if (rc) return rc;
     return truncate_impl(h, st, &kr, nullptr, eps, maxq, out);
 }
@@ -552,8 +559,9 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         !(beta > 0.0) || !(gamma > 0.0) || !(eps > 0.0) || !std::isfinite(beta) ||
         !std::isfinite(gamma))
         return FC_EINVAL;
-    fc_setup_opts opts{1e-10, 24, 32, 48, 0};
+    fc_setup_opts opts{1e-10, 24, 32, 48, 0, 0};
     if (o) {
+        opts.directional = o->directional ? 1 : 0;
         if (o->delta_sym > 0) opts.delta_sym = o->delta_sym;
         if (o->precond_rank > 0) opts.precond_rank = o->precond_rank;
         if (o->max_rank > 0) opts.max_rank = o->max_rank;
@@ -564,14 +572,25 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     opts.max_rank = std::min(opts.max_rank, opts.max_tucker * opts.max_tucker);
     if (opts.max_input_rank <= 0) opts.max_input_rank = opts.max_rank;
     if (int rc_ = ensure_attributes()) return rc_;
+    // Directionally fractional operator sum_l (-Delta_l)^alpha (Remark after Lemma 4.1): the
+    // same eigenbasis with eigenvalues sum_l lambda^alpha, i.e. spectrum lambda^alpha and
+    // exponent 1 in g = beta^2 rho^-1 + gamma rho.
+    std::vector<double> lam = spectrum(n);
+    double alpha_eff = alpha;
+    if (opts.directional) {
+        for (double& x : lam) x = std::pow(x, alpha);
+        alpha_eff = 1.0;
+    }
     SymbolNodes sym, pc;
-    if (!build_control_nodes(n, d, alpha, beta, gamma, opts.delta_sym, sym)) return FC_ESETUP;
-    if (!build_precond_nodes(n, d, alpha, beta, gamma, opts.precond_rank, pc)) return FC_ESETUP;
+    if (!build_control_nodes(lam, d, alpha_eff, beta, gamma, opts.delta_sym, sym)) return FC_ESETUP;
+    if (!build_precond_nodes(lam, d, alpha_eff, beta, gamma, opts.precond_rank, pc)) return FC_ESETUP;
     fc_ctx* h = new (std::nothrow) fc_ctx();
     if (!h) return FC_EINVAL;
     h->n = n; h->d = d; h->alpha = alpha; h->beta = beta; h->gamma = gamma; h->eps = eps;
+    h->alpha_eff = alpha_eff;
     h->opts = opts;
     h->RA = (int)sym.tau.size();
+    h->RS = sym.r_minus;
     h->RP = (int)pc.tau.size();
     h->CAP = opts.max_rank;
     h->KIN = std::max(opts.max_input_rank, opts.max_rank);
@@ -582,7 +601,8 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     // device tables
     const int N = n + 1;
     const int RAm = std::max(h->RA, h->RP);
-    size_t tcount = (size_t)n + 2 * N + h->RA + h->RP + 2 * 3 * (size_t)n * RAm + 2 * 3 * (size_t)n * n;
+    size_t tcount = (size_t)n + 2 * N + h->RA + h->RP + h->RS + 2 * 3 * (size_t)n * RAm +
+                    3 * 3 * (size_t)n * n;
     if (cudaMalloc(&h->tables, tcount * sizeof(double)) != cudaSuccess) {
         delete h;
         return FC_ECUDA;
@@ -596,8 +616,8 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     h->EP = p; p += 3 * (size_t)n * RAm;
     h->GEA = p; p += 3 * (size_t)n * n;
     h->GEP = p; p += 3 * (size_t)n * n;
-    // the symbols use a common mode stride n * RA (EA) so KRIn can address both identically
-    std::vector<double> lam = spectrum(n);
+    h->xiS = p; p += h->RS;
+    h->GES = p; p += 3 * (size_t)n * n;
     std::vector<double> tab(2 * N);
     const double sc = std::sqrt(2.0 / N);
     for (int m = 0; m < 2 * N; ++m) {
@@ -634,6 +654,9 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         const long long nn = (long long)n * n;
         gemm(st, n, n, h->RA, LdSq{h->EA, n, bsE, h->xiA}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GEA, n, nn, d);
         gemm(st, n, n, h->RP, LdSq{h->EP, n, bsP, h->xiP}, LdT{h->EP, n, bsP}, 1.0, 0.0, h->GEP, n, nn, d);
+        // state symbol beta rho^-alpha = (beta^2 rho^-alpha part of the control symbol) / beta
+        launch_copy_weights(st, h->RS, h->xiA, 1.0 / beta, h->xiS);
+        gemm(st, n, n, h->RS, LdSq{h->EA, n, bsE, h->xiS}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GES, n, nn, d);
         if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { rc = FC_ECUDA; break; }
     } while (0);
     cudaFree(dtau); cudaFree(dw); cudaFree(dmode);
@@ -683,13 +706,13 @@ int fc_set_workspace(fc_handle h, void* dev_ptr, size_t bytes) {
 }
 
 int fc_get_symbol(fc_handle h, int which, fc_cp* out, void* stream) {
-    if (!h || !out || !(which == 0 || which == 1) || !check_cp(h, out, true)) return FC_EINVAL;
-    const int R = which ? h->RP : h->RA;
+    if (!h || !out || !(which >= 0 && which <= 2) || !check_cp(h, out, true)) return FC_EINVAL;
+    const int R = which == 1 ? h->RP : (which == 2 ? h->RS : h->RA);
     if (out->cap < R) { out->rank = R; return FC_ERANK; }
     cudaStream_t st = (cudaStream_t)stream;
-    const double* xi = which ? h->xiP : h->xiA;
-    const double* E = which ? h->EP : h->EA;
-    const long long bs = (long long)h->n * R;
+    const double* xi = which == 1 ? h->xiP : (which == 2 ? h->xiS : h->xiA);
+    const double* E = which == 1 ? h->EP : h->EA;
+    const long long bs = (long long)h->n * (which == 1 ? h->RP : h->RA);
     CK(cudaMemcpyAsync(out->xi, xi, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
     for (int l = 0; l < h->d; ++l)
         CK(cudaMemcpy2DAsync(out->U[l], sizeof(double) * out->ld, E + l * bs, sizeof(double) * h->n,
@@ -708,7 +731,7 @@ static int apply_common(fc_handle h, const fc_cp* x, fc_cp* y, void* stream, boo
     cudaStream_t st = (cudaStream_t)stream;
     CP xc = from_user(x);
     KRIn kr;
-    int rc = kr_from(h, st, xc, precond, kr);
+    int rc = kr_from(h, st, xc, precond ? 1 : 0, kr);
     if (rc) return rc;
     // y_l = F (E_l[:,k] . Yh_l[:,j]) for all (k, j), weights xa_k xb_j
     LdSine F{h->sintab, 2 * (h->n + 1)};
@@ -756,15 +779,19 @@ int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int norma
     return rc;
 }
 
+int fc_state(fc_handle h, const fc_cp* u, double eps, int max_rank, fc_cp* y, void* stream) {
+    return fc_apply_trunc(h, 2, u, eps, max_rank, y, stream);
+}
+
 int fc_apply_trunc(fc_handle h, int which, const fc_cp* x, double eps, int max_rank, fc_cp* y,
                    void* stream) {
-    if (!h || !(which == 0 || which == 1) || !check_cp(h, x, false) || !check_cp(h, y, true) ||
+    if (!h || !(which >= 0 && which <= 2) || !check_cp(h, x, false) || !check_cp(h, y, true) ||
         !(eps >= 0.0) || max_rank < 1)
         return FC_EINVAL;
     if (!h->ws) return FC_EWORKSPACE;
     if (x->rank > h->KIN) { y->rank = x->rank; return FC_ERANK; }
     CP xc = from_user(x), yc = from_user(y);
-    int rc = kr_trunc(h, (cudaStream_t)stream, xc, which == 1, eps, max_rank, yc);
+    int rc = kr_trunc(h, (cudaStream_t)stream, xc, which, eps, max_rank, yc);
     y->rank = yc.rank;
     return rc;
 }
@@ -829,7 +856,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         R.rank = B.rank;
     }
     auto track = [&](const CP& c) { inf.max_rank_seen = std::max(inf.max_rank_seen, c.rank); ++inf.trunc_calls; };
-    if ((rc = kr_trunc(h, st, R, true, eps, cap, Z))) return rc;           // Z0 = trunc(precond(R0))
+    if ((rc = kr_trunc(h, st, R, 1, eps, cap, Z))) return rc;           // Z0 = trunc(precond(R0))
     track(Z);
     // P0 = Z0
     for (int l = 0; l < h->d; ++l)
@@ -839,7 +866,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     double rz;
     if ((rc = inner_impl(h, st, R, Z, &rz))) return rc;
     for (int k = 0; k < opts.kmax; ++k) {
-        if ((rc = kr_trunc(h, st, P, false, eps, cap, S))) return rc;        // S = trunc(fun(P))
+        if ((rc = kr_trunc(h, st, P, 0, eps, cap, S))) return rc;        // S = trunc(fun(P))
         track(S);
         double ps;
         if ((rc = inner_impl(h, st, P, S, &ps))) return rc;
@@ -862,7 +889,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         inf.relres = rel;
         if (!std::isfinite(rel)) return finish(FC_ENAN);
         if (rel <= opts.tol) return finish(FC_OK);
-        if ((rc = kr_trunc(h, st, R, true, eps, cap, Z))) return rc;          // Z = trunc(precond(R))
+        if ((rc = kr_trunc(h, st, R, 1, eps, cap, Z))) return rc;          // Z = trunc(precond(R))
         track(Z);
         double rzn;
         if ((rc = inner_impl(h, st, R, Z, &rzn))) return rc;
@@ -932,7 +959,7 @@ int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev
     };
     int rc = dst_all(dev_rhs, dev_u);
     if (rc) return rc;
-    launch_full_scale(st, h->d, n, h->lam, h->alpha, h->beta, h->gamma, dev_u);
+    launch_full_scale(st, h->d, n, h->lam, h->alpha_eff, h->beta, h->gamma, dev_u);
     rc = dst_all(dev_u, dev_u);
     if (rc) return rc;
     CKL();

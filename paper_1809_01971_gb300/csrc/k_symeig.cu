@@ -434,9 +434,11 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                 const float app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
                 float cs = 1.0f, sn = 0.0f;
                 int rot = 0;
-                // relative threshold a few FP32 ulps above rounding noise; at most 15
-                // sweeps (quadratic convergence: ~5 suffice for an ordering basis)
-                if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), 1e-36f)) {
+                // relative threshold a few FP32 ulps above rounding noise, with a floor at
+                // 1e-22 of the largest diagonal entry (directions that weak are at the FP64
+                // rounding level of the Gram and are always dropped by the eps rule); at most
+                // 15 sweeps (quadratic convergence: ~5 suffice for an ordering basis)
+                if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), 1e-22f)) {
                     const float th = (aqq - app) / (2.0f * apq);
                     float t;
                     if (fabsf(th) > 1e18f) t = 0.5f / th;

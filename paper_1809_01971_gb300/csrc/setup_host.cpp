@@ -146,9 +146,9 @@ double g_exact(double rho, double alpha, double beta, double gamma) {
     return beta * beta * std::pow(rho, -alpha) + gamma * std::pow(rho, alpha);
 }
 
-bool build_control_nodes(int n, int d, double alpha, double beta, double gamma, double delta,
-                         SymbolNodes& out) {
-    std::vector<double> lam = spectrum(n);
+bool build_control_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
+                         double gamma, double delta, SymbolNodes& out) {
+    const int n = (int)lam.size();
     const double rmin = d * lam[0], rmax = d * lam[n - 1];
     const double B = rmax / rmin;
     out = SymbolNodes();
@@ -238,12 +238,12 @@ static bool lstsq(std::vector<double> A, int m, int k, std::vector<double> b, st
     return true;
 }
 
-bool build_precond_nodes(int n, int d, double alpha, double beta, double gamma, int rank,
-                         SymbolNodes& out) {
+bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
+                         double gamma, int rank, SymbolNodes& out) {
     // Fit p(rho) = sum_k w_k exp(-tau_k rho) to 1/g(rho) by least squares of p*g - 1 on a
     // geometric grid of [rho_min, rho_max], nodes tau_k geometric in
     // [0.2/rho_max, 20/rho_min]; columns scaled to unit norm before the solve.
-    std::vector<double> lam = spectrum(n);
+    const int n = (int)lam.size();
     const double rmin = d * lam[0], rmax = d * lam[n - 1];
     out = SymbolNodes();
     out.rho_min = rmin;

@@ -31,9 +31,11 @@ struct SymbolNodes {
 std::vector<double> spectrum(int n);
 ExpSum exp_sum(double s, double B, double delta, double s0);
 double g_exact(double rho, double alpha, double beta, double gamma);
-bool build_control_nodes(int n, int d, double alpha, double beta, double gamma, double delta,
-                         SymbolNodes& out);
-bool build_precond_nodes(int n, int d, double alpha, double beta, double gamma, int rank,
-                         SymbolNodes& out);
+// The 1D spectrum lam (ascending) is passed in: lambda_k of the Laplacian, or lambda_k^alpha
+// for the directionally fractional operator (which then uses exponent 1).
+bool build_control_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
+                         double gamma, double delta, SymbolNodes& out);
+bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
+                         double gamma, int rank, SymbolNodes& out);
 
 }  // namespace fc

@@ -42,7 +42,7 @@ class fc_cp(C.Structure):
 
 class fc_setup_opts(C.Structure):
     _fields_ = [("delta_sym", C.c_double), ("precond_rank", C.c_int), ("max_rank", C.c_int),
-                ("max_tucker", C.c_int), ("max_input_rank", C.c_int)]
+                ("max_tucker", C.c_int), ("max_input_rank", C.c_int), ("directional", C.c_int)]
 
 
 class fc_setup_info(C.Structure):
@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
             "fc_truncate": (I, [P, cp_p, D, I, I, cp_p, V]),
             "fc_inner": (I, [P, cp_p, cp_p, C.POINTER(D), V]),
             "fc_apply_trunc": (I, [P, I, cp_p, D, I, cp_p, V]),
+            "fc_state": (I, [P, cp_p, D, I, cp_p, V]),
             "fc_solve": (I, [P, cp_p, cp_p, C.POINTER(fc_solve_opts), C.POINTER(fc_solve_info), V]),
             "fc_solve_batched": (I, [I, C.POINTER(P), cp_p, cp_p, C.POINTER(fc_solve_opts),
                                      C.POINTER(fc_solve_info), C.POINTER(V)]),
@@ -182,6 +183,7 @@ class Handle:
     """A set-up problem (fc_setup) with its torch-allocated workspace bound."""
 
     def __init__(self, ptr: int, device):
+        self.device = device
         self.ptr = C.c_void_p(ptr)
         info = fc_setup_info()
         _check("fc_get_info", lib().fc_get_info(self.ptr, C.byref(info)))
@@ -214,8 +216,9 @@ class Handle:
 
 
 def fc_setup(n, d, alpha, beta, gamma, eps, delta_sym=0.0, precond_rank=0, max_rank=0,
-             max_tucker=0, max_input_rank=0, device="cuda") -> Handle:
-    o = fc_setup_opts(delta_sym, precond_rank, max_rank, max_tucker, max_input_rank)
+             max_tucker=0, max_input_rank=0, directional=False, device="cuda") -> Handle:
+    o = fc_setup_opts(delta_sym, precond_rank, max_rank, max_tucker, max_input_rank,
+                      1 if directional else 0)
     out = C.c_void_p()
     _check("fc_setup", lib().fc_setup(int(n), int(d), float(alpha), float(beta), float(gamma),
                                       float(eps), C.byref(o), C.byref(out)))
@@ -262,6 +265,15 @@ def fc_apply_trunc(h: Handle, which: int, x: CP, eps: float, max_rank: int, y: C
                               C.byref(cy), _stream(stream))
     y.rank = cy.rank
     _check("fc_apply_trunc", rc)
+    return y
+
+
+def fc_state(h: Handle, u: CP, eps: float, max_rank: int, y: CP, stream=None) -> CP:
+    """y = trunc(beta A^-alpha u, eps): the state of the control problem (eqn:State)."""
+    cu, cy = u.desc(), y.desc()
+    rc = lib().fc_state(h.ptr, C.byref(cu), float(eps), int(max_rank), C.byref(cy), _stream(stream))
+    y.rank = cy.rank
+    _check("fc_state", rc)
     return y
 
 
