@@ -340,7 +340,10 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         launch_sumsq(st, (int)K, dn->w, w.scal + 4, 1);
     }
     CKL();
-    launch_gjacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC, false);
+    // the Khatri-Rao Rayleigh-Ritz matrix comes from the n x n Hadamard Gram (normwise
+    // accurate); the dense one from the projected rows (row-graded)
+    launch_gjacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC, false,
+                   kr ? 1e-15f : 1e-20f);
     // Zc_l = Q_l Vr_l (all cs Ritz directions, descending)
     gemm(st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
     // B2_l = Zc_l^T U_l (cs x K, unweighted): its first r_l rows are the projected factors C_l

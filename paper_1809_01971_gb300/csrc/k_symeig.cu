@@ -351,7 +351,7 @@ symeig_kernel(const double* __restrict__ A, int lda, long long bsA, const int* _
 __global__ void __launch_bounds__(kEigThreads)
 gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* __restrict__ dims,
                int dstride, int cmax, double* __restrict__ ev, long long bsE,
-               double* __restrict__ V, int ldv, long long bsV, int rq, int prof)
+               double* __restrict__ V, int ldv, long long bsV, int rq, float floorRel, int prof)
 {
     extern __shared__ double sm[];
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -435,10 +435,11 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                 float cs = 1.0f, sn = 0.0f;
                 int rot = 0;
                 // relative threshold a few FP32 ulps above rounding noise, with a floor at
-                // 1e-22 of the largest diagonal entry (directions that weak are at the FP64
-                // rounding level of the Gram and are always dropped by the eps rule); at most
-                // 15 sweeps (quadratic convergence: ~5 suffice for an ordering basis)
-                if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), 1e-22f)) {
+                // floorRel of the largest diagonal entry: the rounding level of the FP64 Gram
+                // (1e-15 for a Gram formed normwise, ~1e-20 for a row-graded one), below which
+                // entries carry no information; at most 15 sweeps (quadratic convergence:
+                // ~5 suffice for an ordering basis)
+                if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), floorRel)) {
                     const float th = (aqq - app) / (2.0f * apq);
                     float t;
                     if (fabsf(th) > 1e18f) t = 0.5f / th;
@@ -562,13 +563,13 @@ size_t gjacobi_smem() {
 
 void launch_gjacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
                     const int* dims, int dstride, int cmax, double* ev, long long bsE,
-                    double* V, int ldv, long long bsV, bool rq)
+                    double* V, int ldv, long long bsV, bool rq, float floorRel)
 {
     if (batch <= 0) return;
     const bool prof = prof_active(KC_JACOBI);
     ProfMark mark;
     if (prof) prof_begin(st, mark);
-    note_launch(); gjacobi_kernel<<<batch, kEigThreads, gjacobi_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, rq ? 1 : 0, prof ? 1 : 0);
+    note_launch(); gjacobi_kernel<<<batch, kEigThreads, gjacobi_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, rq ? 1 : 0, floorRel, prof ? 1 : 0);
     if (prof) prof_end(st, mark);
 }
 
