@@ -117,12 +117,19 @@ struct fc_ctx {
     double *xiS = nullptr, *GES = nullptr;
     int RS = 0;
     double alpha_eff = 0.0;   // exponent of the symbol's spectrum (1 for the directional operator)
+    // compressed mode factors of the three symbols (operator, preconditioner, state):
+    // Et[s] (3 modes x n x rE[s]) and Mt[s] (3 modes x rE[s] x R_s), see compress_factor
+    double* ctab = nullptr;
+    double *Et[3] = {nullptr, nullptr, nullptr}, *Mt[3] = {nullptr, nullptr, nullptr};
+    int rE[3] = {0, 0, 0};
+    int rEmax = 0;
+    double* ones = nullptr;   // max(kMaxC, rEmax) ones (weights of the compressed columns)
     // workspace (caller-owned)
     char* ws = nullptr;
     size_t ws_bytes = 0;
     // workspace slices
     struct {
-        double *Y, *Y2, *Q, *tmp, *M, *Tm, *GY, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *wK;
+        double *Y, *Y2, *Q, *tmp, *M, *Tm, *GY, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *wK, *C2, *wKt;
         double *core, *G3, *ev3, *W3, *Srot, *SG, *mus, *Vs, *sigma, *X, *Yh;
         double *scal, *Mi;
         int *dims, *tslice, *tidx;
@@ -161,6 +168,8 @@ size_t layout(fc_ctx* h, Arena& a) {
     w.Zr = a.d(3 * nC);
     w.C = a.d(3 * (size_t)std::max(RM, CM) * K);
     w.wK = a.d((size_t)K);
+    w.C2 = a.d(3 * (size_t)CM * std::max<long long>(1, (long long)h->rEmax * h->KIN));
+    w.wKt = a.d(std::max<long long>(1, (long long)h->rEmax * h->KIN));
     w.core = a.d((size_t)RM * RM * RM);
     w.G3 = a.d((size_t)RM * RM);
     w.ev3 = a.d((size_t)RM);
@@ -209,6 +218,63 @@ int ensure_attributes() {
     return FC_OK;
 }
 
+// Compressed mode factors of the operator, preconditioner and state symbols (cold path):
+// the factors built on the device are read back, compressed on the host in FP64
+// (compress_factor, relative tolerance 1e-12 per mode) and uploaded as Et / Mt.
+int compress_symbols(fc_ctx* h) {
+    const int n = h->n, d = h->d;
+    const int Rs[3] = {h->RA, h->RP, h->RS};
+    const double* Edev[3] = {h->EA, h->EP, h->EA};
+    const long long bsE[3] = {(long long)n * h->RA, (long long)n * h->RP, (long long)n * h->RA};
+    const double* xdev[3] = {h->xiA, h->xiP, h->xiS};
+    std::vector<Compressed> comp(3 * d);
+    for (int sy = 0; sy < 3; ++sy) {
+        const int R = Rs[sy];
+        std::vector<double> E((size_t)n * R), xa(R);
+        CK(cudaMemcpy(xa.data(), xdev[sy], sizeof(double) * R, cudaMemcpyDeviceToHost));
+        for (int l = 0; l < d; ++l) {
+            CK(cudaMemcpy(E.data(), Edev[sy] + l * bsE[sy], sizeof(double) * n * R,
+                          cudaMemcpyDeviceToHost));
+            if (!compress_factor(E.data(), n, R, xa.data(), 1e-12, comp[sy * d + l])) return FC_ESETUP;
+        }
+    }
+    size_t total = 0;
+    for (int sy = 0; sy < 3; ++sy) {
+        int r = 0;
+        for (int l = 0; l < d; ++l) r = std::max(r, comp[sy * d + l].r);
+        h->rE[sy] = r;
+        h->rEmax = std::max(h->rEmax, r);
+        total += 3 * ((size_t)n * r + (size_t)r * Rs[sy]);
+    }
+    const size_t nones = std::max(kMaxC, h->rEmax);
+    total += nones;
+    if (cudaMalloc(&h->ctab, total * sizeof(double)) != cudaSuccess) return FC_ECUDA;
+    CK(cudaMemset(h->ctab, 0, total * sizeof(double)));
+    double* p = h->ctab;
+    h->ones = p;
+    p += nones;
+    std::vector<double> ones(nones, 1.0);
+    CK(cudaMemcpy(h->ones, ones.data(), sizeof(double) * nones, cudaMemcpyHostToDevice));
+    for (int sy = 0; sy < 3; ++sy) {
+        const int r = h->rE[sy], R = Rs[sy];
+        h->Et[sy] = p; p += 3 * (size_t)n * r;
+        h->Mt[sy] = p; p += 3 * (size_t)r * R;
+        for (int l = 0; l < d; ++l) {
+            const Compressed& c = comp[sy * d + l];   // zero-padded to r columns / rows
+            std::vector<double> Et((size_t)n * r, 0.0), Mt((size_t)r * R, 0.0);
+            for (int a = 0; a < c.r; ++a)
+                for (int i = 0; i < n; ++i) Et[i + (size_t)a * n] = c.Et[i + (size_t)a * n];
+            for (int k = 0; k < R; ++k)
+                for (int a = 0; a < c.r; ++a) Mt[a + (size_t)k * r] = c.Mt[a + (size_t)k * c.r];
+            CK(cudaMemcpy(h->Et[sy] + (size_t)l * n * r, Et.data(), sizeof(double) * n * r,
+                          cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->Mt[sy] + (size_t)l * r * R, Mt.data(), sizeof(double) * r * R,
+                          cudaMemcpyHostToDevice));
+        }
+    }
+    return FC_OK;
+}
+
 CP from_user(const fc_cp* x) {
     CP c;
     c.rank = x->rank; c.cap = x->cap; c.ld = x->ld; c.xi = x->xi;
@@ -236,6 +302,10 @@ void dst_cols(fc_ctx* h, cudaStream_t st, int cols, const double* const in[3], i
 struct KRIn {           // implicit Khatri-Rao tensor sum_{k,j} xa_k xb_j (x)_l E_l[:,k].Yh_l[:,j]
     const double* xa; const double* E; int Ra; long long bsE; const double* GE;
     const double* xb; const double* Yh; int S;
+    // compressed symbol factors E_l ~ Et_l Mt_l (Et_l: n x rE, Mt_l: rE x Ra, mode strides
+    // bsEt, bsMt); Et_l has the same Gram as E_l diag|xa|, so the Khatri-Rao tensor's side
+    // matrices have the same Gram as those of Et_l . (Yh_l diag|xb|) with rE * S columns
+    const double* Et; long long bsEt; const double* Mt; long long bsMt; int rE;
 };
 struct DenseIn { const double* w; const double* U; int ld; long long bs; int K; };
 
@@ -254,10 +324,13 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     if (K <= 0) { out.rank = 0; return FC_OK; }
     if (K > h->KMAX) return FC_ERANK;
     maxq = std::min(maxq, std::min(out.cap, h->QMAX));
-    // Sketch: K <= CM explicit columns (c = cs = K); otherwise CM random columns, of which the
-    // first cs = CM - kHold span the basis and the last kHold estimate the energy it misses.
-    const bool sketch = K > CM;
-    const int c = sketch ? CM : (int)K;
+    // Stage 1 sees the side matrices through a matrix with the same Gram: the explicit
+    // columns, or for a mat-vec output the compressed Khatri-Rao matrix (Kt = rE * S columns).
+    const long long Kt = kr ? (long long)kr->rE * kr->S : K;
+    // Sketch: Kt <= CM explicit columns (c = cs = Kt); otherwise CM random columns, of which
+    // the first cs = CM - kHold span the basis and the last kHold estimate the energy it misses.
+    const bool sketch = Kt > CM;
+    const int c = sketch ? CM : (int)Kt;
     const int cs = sketch ? CM - kHold : c;
     const unsigned long long seed = (h->seed += 0x9E3779B97F4A7C15ull);
     int* dims = w.dims;
@@ -267,10 +340,10 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     // ---- stage 1: range of the weighted side matrices W_l = U_l diag|w| ------------------
     if (kr) {
         if (!sketch)
-            launch_kr_cols(st, d, n, kr->Ra, kr->S, kr->E, n, kr->bsE, kr->xa,
+            launch_kr_cols(st, d, n, kr->rE, kr->S, kr->Et, n, kr->bsEt, nullptr,
                            kr->Yh, n, (long long)n * h->KIN, kr->xb, 1, w.Y, n, nC);
         else
-            launch_sketch_kr(st, d, n, kr->Ra, kr->S, c, kr->E, n, kr->bsE, kr->xa,
+            launch_sketch_kr(st, d, n, kr->rE, kr->S, c, kr->Et, n, kr->bsEt, nullptr,
                              kr->Yh, n, (long long)n * h->KIN, kr->xb, seed, w.Y, n, nC, w.tmp);
     } else {
         if (!sketch)
@@ -350,19 +423,33 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     // of the core; rho_i = sum_K w_K^2 B2[i, K]^2 is the energy of W_l along Ritz direction i
     const long long RK = (long long)CM * K;
     const double* wK = dn ? dn->w : w.wK;
-    if (kr)
-        gemm(st, cs, (int)K, n, LdT{w.Z, n, nC},
-             LdKR{kr->E, n, kr->bsE, kr->Yh, n, (long long)n * h->KIN, kr->S}, 1.0, 0.0, w.C, CM,
-             RK, d);
-    else
+    if (kr) {
+        // B2t_l = Zc_l^T (Et_l . Yh_l) (cs x rE S); energies from its rows with weights |xb|
+        const long long RKt = (long long)CM * Kt;
+        gemm(st, cs, (int)Kt, n, LdT{w.Z, n, nC},
+             LdKR{kr->Et, n, kr->bsEt, kr->Yh, n, (long long)n * h->KIN, kr->S}, 1.0, 0.0, w.C2, CM,
+             RKt, d);
+        launch_outer_weights(st, kr->rE, h->ones, kr->S, kr->xb, w.wKt);
+        launch_row_energy(st, d, cs, (int)Kt, w.C2, CM, RKt, w.wKt, w.theta, CM);
+    } else {
         gemm(st, cs, (int)K, n, LdT{w.Z, n, nC}, LdN{dn->U, dn->ld, dn->bs}, 1.0, 0.0, w.C, CM, RK,
              d);
-    launch_row_energy(st, d, cs, (int)K, w.C, CM, RK, wK, w.theta, CM);
+        launch_row_energy(st, d, cs, (int)K, w.C, CM, RK, wK, w.theta, CM);
+    }
     // Tucker ranks: smallest r_l with sum_{i >= r_l} rho_i + missed <= (eps ||w||_2)^2 / (2d)
     launch_select_tucker(st, d, w.theta, CM, w.scal + 24, w.scal + 4, eps * eps / (2.0 * d),
                          std::min(RM, cs), dims + D_R, w.scal + 8, dims + D_C1);
     launch_stage2_dims(st, d, dims);
     const int rz = std::min(RM, cs);
+    if (kr) {
+        // projected factors of the actual terms: C_l[:, (k,j)] = sum_a B2t_l[:, (a,j)] Mt_l[a,k]
+        // (first r_l rows), one GEMM per mode batched over the S input columns j
+        const long long RKt = (long long)CM * Kt;
+        for (int l = 0; l < d; ++l)
+            gemm(st, cs, kr->Ra, kr->rE, LdColsJ{w.C2 + l * RKt, CM, kr->S},
+                 LdN{kr->Mt + l * kr->bsMt, kr->rE, 0}, 1.0, 0.0, w.C + l * RK, CM * kr->S, CM,
+                 kr->S, dims + D_R + l);
+    }
     CKL();
     // ---- core: B3[(a + r0 b), c] = sum_K w_K C0[a,K] C1[b,K] C2[c,K] ----------------------
     const int RR = RM * RM;
@@ -433,6 +520,12 @@ int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, int which, KRIn& kr) {
     } else {
         kr.xa = h->xiA; kr.E = h->EA; kr.Ra = h->RA; kr.bsE = (long long)h->n * h->RA; kr.GE = h->GEA;
     }
+    const int sidx = (which == 1) ? 1 : (which == 2 ? 2 : 0);
+    kr.rE = h->rE[sidx];
+    kr.Et = h->Et[sidx];
+    kr.bsEt = (long long)h->n * kr.rE;
+    kr.Mt = h->Mt[sidx];
+    kr.bsMt = (long long)kr.rE * kr.Ra;
     kr.xb = x.xi;
     kr.Yh = h->w.Yh;
     kr.S = x.rank;
@@ -663,6 +756,7 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { rc = FC_ECUDA; break; }
     } while (0);
     cudaFree(dtau); cudaFree(dw); cudaFree(dmode);
+    if (rc == FC_OK) rc = compress_symbols(h);
     if (rc == FC_OK && (cudaMallocHost(&h->hbuf, 64 * sizeof(double)) != cudaSuccess ||
                         cudaMallocHost(&h->hint, 64 * sizeof(int)) != cudaSuccess))
         rc = FC_ECUDA;
@@ -973,6 +1067,7 @@ int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev
 void fc_destroy(fc_handle h) {
     if (!h) return;
     if (h->tables) cudaFree(h->tables);
+    if (h->ctab) cudaFree(h->ctab);
     if (h->hbuf) cudaFreeHost(h->hbuf);
     if (h->hint) cudaFreeHost(h->hint);
     delete h;

@@ -96,6 +96,12 @@ struct LdCore {
         return w[k] * C0[a + (long long)k * ldc] * C1[b + (long long)k * ldc];
     }
 };
+// columns (k*S + b) of a column-major matrix, batch item b (the input column j of a
+// Khatri-Rao product): element (i, k) of batch b = p[i + (k*S + b)*ld]
+struct LdColsJ {
+    const double* p; int ld; int S;
+    FC_DEV double operator()(int i, int k, int b) const { return p[i + ((long long)k * S + b) * ld]; }
+};
 struct LdOnes { FC_DEV double operator()(int, int, int) const { return 1.0; } };
 struct LdPart {   // sum of S partial results (split-K reduction), element i
     const double* p; int S; long long stride;

@@ -126,6 +126,7 @@ __global__ void kr_cols_kernel(int n, int Ra, int S, const double* E, int lde, l
         int k = kj / S, j = kj - k * S;
         double s = 1.0;
         if (xa) s = absw ? fabs(xa[k] * xb[j]) : xa[k] * xb[j];
+        else if (xb) s = absw ? fabs(xb[j]) : xb[j];
         Y[l * bsO + i + (long long)kj * ldo] =
             s * E[l * bsE + i + (long long)k * lde] * Yh[l * bsY + i + (long long)j * ldy];
     }

@@ -288,4 +288,71 @@ bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, do
     return true;
 }
 
+bool compress_factor(const double* E, int n, int R, const double* xa, double tol, Compressed& out) {
+    out = Compressed();
+    if (n <= 0 || R <= 0) return false;
+    std::vector<double> X((size_t)n * R), V((size_t)R * R, 0.0), nrm(R);
+    for (int k = 0; k < R; ++k) {
+        const double s = std::fabs(xa[k]);
+        for (int i = 0; i < n; ++i) X[i + (size_t)k * n] = E[i + (size_t)k * n] * s;
+        V[k + (size_t)k * R] = 1.0;
+    }
+    auto dot = [&](int p, int q) {
+        double s = 0.0;
+        const double* a = &X[(size_t)p * n];
+        const double* b = &X[(size_t)q * n];
+        for (int i = 0; i < n; ++i) s += a[i] * b[i];
+        return s;
+    };
+    for (int k = 0; k < R; ++k) nrm[k] = dot(k, k);
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < R; ++p)
+            for (int q = p + 1; q < R; ++q) {
+                const double a = nrm[p], b = nrm[q];
+                if (a == 0.0 || b == 0.0) continue;
+                const double g = dot(p, q);
+                if (std::fabs(g) <= 1e-15 * std::sqrt(a * b)) continue;
+                rotated = true;
+                const double zeta = (b - a) / (2.0 * g);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                double* xp = &X[(size_t)p * n];
+                double* xq = &X[(size_t)q * n];
+                for (int i = 0; i < n; ++i) {
+                    const double u = xp[i], w = xq[i];
+                    xp[i] = c * u - s * w;
+                    xq[i] = s * u + c * w;
+                }
+                double* vp = &V[(size_t)p * R];
+                double* vq = &V[(size_t)q * R];
+                for (int i = 0; i < R; ++i) {
+                    const double u = vp[i], w = vq[i];
+                    vp[i] = c * u - s * w;
+                    vq[i] = s * u + c * w;
+                }
+                nrm[p] = dot(p, p);
+                nrm[q] = dot(q, q);
+            }
+        if (!rotated) break;
+    }
+    std::vector<int> idx(R);
+    for (int k = 0; k < R; ++k) idx[k] = k;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return nrm[a] > nrm[b]; });
+    const double smax = std::sqrt(nrm[idx[0]]);
+    if (!(smax > 0.0)) return false;
+    int r = 0;
+    while (r < R && std::sqrt(nrm[idx[r]]) > tol * smax) ++r;
+    out.r = r;
+    out.Et.assign((size_t)n * r, 0.0);
+    out.Mt.assign((size_t)r * R, 0.0);
+    for (int a = 0; a < r; ++a) {
+        const int k = idx[a];
+        for (int i = 0; i < n; ++i) out.Et[i + (size_t)a * n] = X[i + (size_t)k * n];
+        for (int j = 0; j < R; ++j)
+            out.Mt[a + (size_t)j * r] = (xa[j] != 0.0) ? V[j + (size_t)k * R] / std::fabs(xa[j]) : 0.0;
+    }
+    return true;
+}
+
 }  // namespace fc

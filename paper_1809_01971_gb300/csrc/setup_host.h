@@ -38,4 +38,16 @@ bool build_control_nodes(const std::vector<double>& lam, int d, double alpha, do
 bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
                          double gamma, int rank, SymbolNodes& out);
 
+// Compressed mode factor of a CP symbol: with X = E diag|xa| (n x R, E column-major with unit
+// columns) and its thin SVD X = U S V^T truncated to the r singular values above tol * S_max,
+//   Et = U S = X V_r  (n x r),   Mt = V_r^T diag(1/|xa|)  (r x R),
+// so that E ~ Et Mt (weighted error sqrt(sum_{i>r} s_i^2)) and Mt diag(xa^2) Mt^T = I.
+// The SVD is a one-sided (Hestenes) Jacobi on the columns of X, in FP64.
+struct Compressed {
+    int r = 0;
+    std::vector<double> Et;   // n x r
+    std::vector<double> Mt;   // r x R
+};
+bool compress_factor(const double* E, int n, int R, const double* xa, double tol, Compressed& out);
+
 }  // namespace fc
