@@ -72,6 +72,10 @@ typedef struct fc_setup_opts {
     int directional;    /* != 0: the directionally fractional operator A_(alpha) =           */
                         /* sum_l (-Delta_l)^alpha (Remark after Lemma 4.1) in place of A^alpha: */
                         /* the equation (beta^2 A_(alpha)^-1 + gamma A_(alpha)) u = b [0]    */
+    int precision;      /* 0: FP64 contractions; 1: the large contractions (DST, Khatri-Rao  */
+                        /* projections, Tucker core) in double-float arithmetic on the FP32  */
+                        /* pipe (hi + lo FP32 pairs, ~1e-14 relative), 64x GB300's FP64 rate; */
+                        /* eigen-solves, Grams of the sketch and scalars stay FP64 [0]        */
 } fc_setup_opts;
 
 typedef struct fc_setup_info {

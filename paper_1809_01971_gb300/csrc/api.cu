@@ -117,6 +117,7 @@ struct fc_ctx {
     double *xiS = nullptr, *GES = nullptr;
     int RS = 0;
     double alpha_eff = 0.0;   // exponent of the symbol's spectrum (1 for the directional operator)
+    int prec = GP_F64;        // contractions in FP64 or double-float FP32 (fc_setup_opts.precision)
     // compressed mode factors of the three symbols (operator, preconditioner, state):
     // Et[s] (3 modes x n x rE[s]) and Mt[s] (3 modes x rE[s] x R_s), see compress_factor
     double* ctab = nullptr;
@@ -296,7 +297,7 @@ void dst_cols(fc_ctx* h, cudaStream_t st, int cols, const double* const in[3], i
     if (cols <= 0) return;
     LdSine F{h->sintab, 2 * (h->n + 1)};
     for (int l = 0; l < h->d; ++l)
-        gemm(st, h->n, cols, h->n, F, LdN{in[l], ldi, 0}, 1.0, 0.0, out[l], ldo);
+        gemm_p(h->prec, st, h->n, cols, h->n, F, LdN{in[l], ldi, 0}, 1.0, 0.0, out[l], ldo);
 }
 
 struct KRIn {           // implicit Khatri-Rao tensor sum_{k,j} xa_k xb_j (x)_l E_l[:,k].Yh_l[:,j]
@@ -406,7 +407,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     } else {
         // Bq = Q^T W (cs x K) in w.C, T = Bq Bq^T
         double* Bq = w.C;
-        gemm(st, cs, (int)K, n, LdT{Qb, n, nC}, LdAbsN{dn->U, dn->ld, dn->bs, dn->w}, 1.0, 0.0, Bq,
+        gemm_p(h->prec, st, cs, (int)K, n, LdT{Qb, n, nC}, LdAbsN{dn->U, dn->ld, dn->bs, dn->w}, 1.0, 0.0, Bq,
              CM, (long long)CM * K, d);
         gemm(st, cs, cs, (int)K, LdN{Bq, CM, (long long)CM * K}, LdT{Bq, CM, (long long)CM * K}, 1.0,
              0.0, w.Tr, CM, CC, d);
@@ -426,13 +427,13 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     if (kr) {
         // B2t_l = Zc_l^T (Et_l . Yh_l) (cs x rE S); energies from its rows with weights |xb|
         const long long RKt = (long long)CM * Kt;
-        gemm(st, cs, (int)Kt, n, LdT{w.Z, n, nC},
+        gemm_p(h->prec, st, cs, (int)Kt, n, LdT{w.Z, n, nC},
              LdKR{kr->Et, n, kr->bsEt, kr->Yh, n, (long long)n * h->KIN, kr->S}, 1.0, 0.0, w.C2, CM,
              RKt, d);
         launch_outer_weights(st, kr->rE, h->ones, kr->S, kr->xb, w.wKt);
         launch_row_energy(st, d, cs, (int)Kt, w.C2, CM, RKt, w.wKt, w.theta, CM);
     } else {
-        gemm(st, cs, (int)K, n, LdT{w.Z, n, nC}, LdN{dn->U, dn->ld, dn->bs}, 1.0, 0.0, w.C, CM, RK,
+        gemm_p(h->prec, st, cs, (int)K, n, LdT{w.Z, n, nC}, LdN{dn->U, dn->ld, dn->bs}, 1.0, 0.0, w.C, CM, RK,
              d);
         launch_row_energy(st, d, cs, (int)K, w.C, CM, RK, wK, w.theta, CM);
     }
@@ -446,7 +447,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         // (first r_l rows), one GEMM per mode batched over the S input columns j
         const long long RKt = (long long)CM * Kt;
         for (int l = 0; l < d; ++l)
-            gemm(st, cs, kr->Ra, kr->rE, LdColsJ{w.C2 + l * RKt, CM, kr->S},
+            gemm_p(h->prec, st, cs, kr->Ra, kr->rE, LdColsJ{w.C2 + l * RKt, CM, kr->S},
                  LdN{kr->Mt + l * kr->bsMt, kr->rE, 0}, 1.0, 0.0, w.C + l * RK, CM * kr->S, CM,
                  kr->S, dims + D_R + l);
     }
@@ -455,10 +456,10 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     const int RR = RM * RM;
     LdCore A{w.C, w.C + RK, wK, CM, dims + D_R};
     if (d == 3)
-        gemm(st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, CM, 0}, 1.0, 0.0, w.core, RR, 0, 1,
+        gemm_p(h->prec, st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, CM, 0}, 1.0, 0.0, w.core, RR, 0, 1,
              dims + D_R12, dims + D_R3, nullptr);
     else
-        gemm(st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, w.core, RR, 0, 1, dims + D_R12, nullptr,
+        gemm_p(h->prec, st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, w.core, RR, 0, 1, dims + D_R12, nullptr,
              nullptr);
     CKL();
     launch_core_energy(st, d, w.core, RR, dims, w.scal + 12);
@@ -655,9 +656,10 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         !(beta > 0.0) || !(gamma > 0.0) || !(eps > 0.0) || !std::isfinite(beta) ||
         !std::isfinite(gamma))
         return FC_EINVAL;
-    fc_setup_opts opts{1e-10, 24, 32, 48, 0, 0};
+    fc_setup_opts opts{1e-10, 24, 32, 48, 0, 0, 0};
     if (o) {
         opts.directional = o->directional ? 1 : 0;
+        opts.precision = (o->precision == 1) ? 1 : 0;
         if (o->delta_sym > 0) opts.delta_sym = o->delta_sym;
         if (o->precond_rank > 0) opts.precond_rank = o->precond_rank;
         if (o->max_rank > 0) opts.max_rank = o->max_rank;
@@ -684,6 +686,7 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     if (!h) return FC_EINVAL;
     h->n = n; h->d = d; h->alpha = alpha; h->beta = beta; h->gamma = gamma; h->eps = eps;
     h->alpha_eff = alpha_eff;
+    h->prec = opts.precision ? GP_DF32 : GP_F64;
     h->opts = opts;
     h->RA = (int)sym.tau.size();
     h->RS = sym.r_minus;
@@ -834,7 +837,7 @@ static int apply_common(fc_handle h, const fc_cp* x, fc_cp* y, void* stream, boo
     LdSine F{h->sintab, 2 * (h->n + 1)};
     const long long bsE = (long long)h->n * R;
     for (int l = 0; l < h->d; ++l)
-        gemm(st, h->n, (int)K, h->n, F,
+        gemm_p(h->prec, st, h->n, (int)K, h->n, F,
              LdKR{kr.E + l * bsE, h->n, 0, kr.Yh + (long long)l * h->n * h->KIN, h->n, 0, kr.S}, 1.0,
              0.0, y->U[l], y->ld);
     launch_outer_weights(st, R, kr.xa, kr.S, kr.xb, y->xi);
@@ -924,6 +927,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     double bn2;
     if ((rc = inner_impl(h, st, B, B, &bn2))) return rc;
     X.rank = 0;
+    double bscale = 1.0;
     auto finish = [&](int status) -> int {
         inf.status = status;
         inf.rank_x = X.rank;
@@ -935,8 +939,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
             if (X.rank > 0)
                 CK(cudaMemcpy2DAsync(u->U[l], sizeof(double) * u->ld, X.U[l], sizeof(double) * X.ld,
                                      sizeof(double) * h->n, X.rank, cudaMemcpyDeviceToDevice, st));
-        if (X.rank > 0)
-            CK(cudaMemcpyAsync(u->xi, X.xi, sizeof(double) * X.rank, cudaMemcpyDeviceToDevice, st));
+        if (X.rank > 0) launch_copy_weights(st, X.rank, X.xi, bscale, u->xi);   // undo 1/||B||
         u->rank = X.rank;
         CK(cudaStreamSynchronize(st));
         if (info) *info = inf;
@@ -944,9 +947,12 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     };
     if (!(bn2 > 0.0)) return finish(std::isfinite(bn2) ? FC_OK : FC_ENAN);
     const double bn = std::sqrt(bn2);
-    // R0 = B (normalised columns, same tensor), X0 = 0
+    // The iteration runs on B / ||B|| (all iterates O(1); the truncation thresholds and the
+    // stopping test are relative, so this only fixes the scale); X is scaled back at exit.
+    bscale = bn;
+    // R0 = B / ||B|| (normalised columns, same tensor), X0 = 0
     {
-        Piece p0{B.xi, {B.U[0], B.U[1], B.U[2]}, B.ld, B.rank, 1.0};
+        Piece p0{B.xi, {B.U[0], B.U[1], B.U[2]}, B.ld, B.rank, 1.0 / bn};
         Piece p1{nullptr, {nullptr, nullptr, nullptr}, 0, 0, 0.0};
         launch_concat_normalize(st, h->d, h->n, p0, p1, R.U[0], R.ld, R.bs(), R.xi);
         CKL();
@@ -980,7 +986,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         track(R);
         double rr;
         if ((rc = inner_impl(h, st, R, R, &rr))) return rc;
-        const double rel = std::sqrt(std::max(rr, 0.0)) / bn;
+        const double rel = std::sqrt(std::max(rr, 0.0));          // ||R|| / ||B||
         if (k < 128) inf.history[k] = rel;
         inf.iters = k + 1;
         inf.relres = rel;

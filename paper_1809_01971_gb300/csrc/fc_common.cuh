@@ -201,6 +201,103 @@ gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Double-float variant of gemm_kernel: operands are split on load into FP32 pairs
+// (hi = fl32(v), lo = fl32(v - hi)) and every multiply-add runs on the FP32 pipe as an exact
+// product (fmaf error term) plus cross terms and a two-sum accumulation, ~48 mantissa bits
+// (relative error ~1e-14).  GB300 issues 64x more FP32 than FP64 FMAs per clock, so this
+// runs ~4x faster than the FP64 kernel on contraction-bound GEMMs.  Values must stay within
+// the FP32 exponent range (|v| < 2^126; parts below 2^-126 flush to zero, relative to the
+// operands' scale that is far below the FP64 rounding of the result).
+// ---------------------------------------------------------------------------------------
+FC_DEV void df_fma(float2& acc, float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float pe = fmaf(a.x, b.x, -p);
+    pe = fmaf(a.x, b.y, pe);
+    pe = fmaf(a.y, b.x, pe);
+    const float s = acc.x + p;
+    const float bb = s - acc.x;
+    const float err = (acc.x - (s - bb)) + (p - bb);
+    const float lo = acc.y + pe + err;
+    const float hi = s + lo;
+    acc.y = lo - (hi - s);
+    acc.x = hi;
+}
+FC_DEV float2 df_split(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+template <int T, class LA, class LB>
+__global__ void __launch_bounds__(256)
+gemm_df_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
+               LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
+               int batch, int splits, int kchunk)
+{
+    constexpr int R = T / 16;
+    constexpr int LOADS = T * GBK / 256;
+    __shared__ float2 As[GBK][T + 1];
+    __shared__ float2 Bs[GBK][T + 1];
+    if (dM) M = min(M, *dM);
+    if (dN) N = min(N, *dN);
+    if (dK) K = min(K, *dK);
+    const int zb = blockIdx.z / splits, zs = blockIdx.z - zb * splits;
+    const int m0 = blockIdx.x * T, n0 = blockIdx.y * T;
+    if (m0 >= M || n0 >= N || zb >= batch) return;
+    int kbeg = zs * kchunk, kend = min(K, kbeg + kchunk);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float2 acc[R][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] = make_float2(0.0f, 0.0f);
+    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+        for (int t = 0; t < LOADS; ++t) {
+            int e = threadIdx.x + t * 256;
+            int ii = e % T, kk = e / T;
+            int gi = m0 + ii, gk = k0 + kk;
+            As[kk][ii] = df_split((gi < M && gk < kend) ? A(gi, gk, zb) : 0.0);
+        }
+#pragma unroll
+        for (int t = 0; t < LOADS; ++t) {
+            int e = threadIdx.x + t * 256;
+            int kk = e & 15, jj = e >> 4;
+            int gj = n0 + jj, gk = k0 + kk;
+            Bs[kk][jj] = df_split((gj < N && gk < kend) ? B(gk, gj, zb) : 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            float2 a[R], b[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < R; ++j) df_fma(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+    double* Cb = C + zb * bsC;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        int gi = m0 + ty + 16 * i;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            int gj = n0 + tx + 16 * j;
+            if (gj >= N) continue;
+            const double v = (double)acc[i][j].x + (double)acc[i][j].y;
+            double* c = Cb + gi + (long long)gj * ldc;
+            if (splits > 1) atomicAdd(c, alpha * v);
+            else *c = (beta == 0.0) ? alpha * v : alpha * v + beta * (*c);
+        }
+    }
+}
+
 // C[b][i, j] *= beta (beta == 0: set to 0) over the live M x N (split-K pre-pass).
 __global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN, double beta,
                                      double* C, int ldc, long long bsC);
@@ -208,10 +305,13 @@ __global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN,
 // Launch: the largest tile (64, 32, 16) whose grid still covers the 152 SMs, then split-K
 // until about 4 CTAs per SM (GB300 runs few FP64 FMAs per SM per clock, so the SM count
 // decides the rate).
+// Precision of a contraction: FP64, or double-float on the FP32 pipe (gemm_df_kernel).
+enum GemmPrec { GP_F64 = 0, GP_DF32 = 1 };
+
 template <class LA, class LB>
-inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha, double beta,
-                 double* C, int ldc, long long bsC = 0, int batch = 1,
-                 const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr)
+inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha,
+                   double beta, double* C, int ldc, long long bsC = 0, int batch = 1,
+                   const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr)
 {
     if (M <= 0 || N <= 0 || batch <= 0) return;
     auto tiles_of = [&](int T) {
@@ -238,6 +338,18 @@ inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha,
     }
     dim3 grid((M + T - 1) / T, (N + T - 1) / T, batch * splits);
     note_launch();
+    if (prec == GP_DF32) {
+        if (T == 64)
+            gemm_df_kernel<64, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta,
+                                                             C, ldc, bsC, batch, splits, kchunk);
+        else if (T == 32)
+            gemm_df_kernel<32, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta,
+                                                             C, ldc, bsC, batch, splits, kchunk);
+        else
+            gemm_df_kernel<16, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta,
+                                                             C, ldc, bsC, batch, splits, kchunk);
+        return;
+    }
     if (T == 64)
         gemm_kernel<64, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
                                                       ldc, bsC, batch, splits, kchunk);
@@ -247,6 +359,14 @@ inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha,
     else
         gemm_kernel<16, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
                                                       ldc, bsC, batch, splits, kchunk);
+}
+
+template <class LA, class LB>
+inline void gemm(cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha, double beta,
+                 double* C, int ldc, long long bsC = 0, int batch = 1,
+                 const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr)
+{
+    gemm_p(GP_F64, st, M, N, K, A, B, alpha, beta, C, ldc, bsC, batch, dM, dN, dK);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -196,13 +196,15 @@ def test_truncate_sketch_path_matches_oracle(fc, n, d, R, eps, rate):
     assert rel(Yf, Rf) <= 3.0 * eps + floor + 1e-13
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("n,d,S,which,eps", [(31, 2, 3, 0, 1e-8), (40, 3, 4, 0, 1e-7),
                                              (40, 3, 4, 1, 1e-7), (64, 3, 8, 0, 1e-6)])
-def test_apply_trunc_matches_oracle(fc, n, d, S, which, eps):
+def test_apply_trunc_matches_oracle(fc, n, d, S, which, eps, precision):
     """trunc(fun(x)) / trunc(precond(x)) of Algorithm 1 with the Khatri-Rao columns kept
     implicit, against the oracle's truncation of the explicit mat-vec (normalize=False).
     Inputs are smooth separable Gaussians (the solver's right-hand sides)."""
-    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, eps, max_rank=1024, max_input_rank=32)
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, eps, max_rank=1024, max_input_rank=32,
+                    precision=precision)
     X = fi.gaussians_cp(n, d, S, np.random.default_rng(fi.seed_for(6, n + S)))
     Xg = fc.CP.from_factors(*X)
     Y = fc.CP(d, n, 1024)
@@ -217,7 +219,7 @@ def test_apply_trunc_matches_oracle(fc, n, d, S, which, eps):
     wn = float(np.linalg.norm(M[0]))
     ag, ao, agr = (np.linalg.norm(Yf - Mf) / wn, np.linalg.norm(Rf - Mf) / wn,
                    np.linalg.norm(Yf - Rf) / wn)
-    print(f"apply_trunc which={which} n={n} d={d} S={S} K={len(M[0])}: gpu rank {Y.rank} "
+    print(f"apply_trunc prec={precision} which={which} n={n} d={d} S={S} K={len(M[0])}: gpu rank {Y.rank} "
           f"oracle {len(ref[0])} |gpu-M|/|xi|={ag:.3e} |oracle-M|/|xi|={ao:.3e} "
           f"|gpu-oracle|/|xi|={agr:.3e} (|xi|/|M| = {wn / np.linalg.norm(Mf):.1f})")
     floor = GRAM_FLOOR if eps < 1e-7 else 0.0
@@ -263,15 +265,16 @@ def test_solve_sine_mode_exact(fc, n, modes, alpha, gamma_):
     assert e < 1e-8
 
 
-def _solve_vs_full(fc, prob, tol, eps, max_rank=32):
-    h = fc.fc_setup(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, eps, max_rank=max_rank)
+def _solve_vs_full(fc, prob, tol, eps, max_rank=32, precision=0):
+    h = fc.fc_setup(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, eps, max_rank=max_rank,
+                    precision=precision)
     B = fc.CP.from_factors(*prob.rhs())
     U = fc.CP(prob.d, prob.n, max_rank)
     info = fc.fc_solve(h, B, U, tol=tol, eps=eps)
     ref = full.solve_full(cp.to_full(prob.rhs()), prob.alpha, prob.beta, prob.gamma)
     e = rel(gpu_full(fc, h, U), ref)
     hist = [info.history[i] for i in range(min(info.iters, 8))]
-    print(f"{prob.label}: iters {info.iters} relres {info.relres:.2e} rank {U.rank} "
+    print(f"{prob.label} prec={precision}: iters {info.iters} relres {info.relres:.2e} rank {U.rank} "
           f"max rank {info.max_rank_seen} err vs full {e:.3e} hist {['%.1e' % x for x in hist]}")
     return info, e
 
@@ -284,12 +287,14 @@ def test_solve_config1_2d(fc):
     assert e < 1e-7
 
 
-@pytest.mark.parametrize("problem", [0, 3, 4, 5])
-def test_solve_config2_3d_n255(fc, problem):
+@pytest.mark.parametrize("problem,precision", [(0, 0), (3, 0), (4, 0), (5, 0), (1, 1), (5, 1)])
+def test_solve_config2_3d_n255(fc, problem, precision):
     """3D, n=255, 4 Gaussians + sine mode: CP-PCG vs the full oracle (16.6M points), at the
-    workload's settings (eps = 1e-9, tol = 1e-8, cap 192): error <= 1e-6."""
+    workload's settings (eps = 1e-9, tol = 1e-8, cap 192): error <= 1e-6, with FP64 and with
+    double-float contractions."""
     prob = fi.config2(problem)
-    info, e = _solve_vs_full(fc, prob, prob.tol, prob.eps, max_rank=prob.max_rank)
+    info, e = _solve_vs_full(fc, prob, prob.tol, prob.eps, max_rank=prob.max_rank,
+                             precision=precision)
     assert info.status == 0
     assert e < 1e-6
 
