@@ -42,8 +42,9 @@ struct LdT {  // op(X) = X^T
 struct LdSine {
     const double* tab; int N2;
     FC_DEV double operator()(int i, int k, int) const {
-        long long m = (long long)(i + 1) * (k + 1);
-        return tab[m % N2];
+        // (i+1)(k+1) <= (n+1)^2 < 2^31 for n <= 4095: 32-bit arithmetic
+        const unsigned m = (unsigned)(i + 1) * (unsigned)(k + 1);
+        return tab[m % (unsigned)N2];
     }
 };
 // Khatri-Rao column (k,j) -> e_k . y_j, column index kj = k*S + j, row i (Section 3.2,
@@ -317,8 +318,11 @@ inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, d
     auto tiles_of = [&](int T) {
         return (long long)((M + T - 1) / T) * ((N + T - 1) / T) * batch;
     };
+    // FP64: the largest tile that still covers the SMs.  Double-float: operand splitting
+    // costs FP64 work per loaded element, so keep 64-wide tiles down to a quarter of the SMs.
     int T = 64;
-    if (tiles_of(64) < kNumSMs) T = (tiles_of(32) < kNumSMs) ? 16 : 32;
+    const long long need = (prec == GP_DF32) ? kNumSMs / 4 : kNumSMs;
+    if (tiles_of(64) < need) T = (tiles_of(32) < need) ? 16 : 32;
     const long long tiles = tiles_of(T);
     int splits = 1;
     if (tiles < 2 * kNumSMs && K >= 128) {

@@ -288,15 +288,52 @@ bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, do
     return true;
 }
 
+// Householder QR of the column-major m x c matrix A (m >= c), in place: returns the upper
+// triangle R (c x c, column-major) of A = Q R.
+static std::vector<double> householder_r(std::vector<double> A, int m, int c) {
+    for (int j = 0; j < c; ++j) {
+        double nrm = 0.0;
+        for (int i = j; i < m; ++i) nrm += A[i + (size_t)j * m] * A[i + (size_t)j * m];
+        nrm = std::sqrt(nrm);
+        if (nrm == 0.0) continue;
+        const double a0 = A[j + (size_t)j * m];
+        const double beta = (a0 >= 0) ? -nrm : nrm;
+        const double v0 = a0 - beta;
+        const double tau = (beta - a0) / beta;
+        for (int i = j + 1; i < m; ++i) A[i + (size_t)j * m] /= v0;
+        A[j + (size_t)j * m] = beta;
+        for (int q = j + 1; q < c; ++q) {
+            double* col = &A[(size_t)q * m];
+            double s = col[j];
+            for (int i = j + 1; i < m; ++i) s += A[i + (size_t)j * m] * col[i];
+            s *= tau;
+            col[j] -= s;
+            for (int i = j + 1; i < m; ++i) col[i] -= s * A[i + (size_t)j * m];
+        }
+    }
+    std::vector<double> R((size_t)c * c, 0.0);
+    for (int q = 0; q < c; ++q)
+        for (int i = 0; i <= q; ++i) R[i + (size_t)q * c] = A[i + (size_t)q * m];
+    return R;
+}
+
 bool compress_factor(const double* E, int n, int R, const double* xa, double tol, Compressed& out) {
     out = Compressed();
     if (n <= 0 || R <= 0) return false;
-    std::vector<double> X((size_t)n * R), V((size_t)R * R, 0.0), nrm(R);
+    std::vector<double> X0((size_t)n * R);
     for (int k = 0; k < R; ++k) {
         const double s = std::fabs(xa[k]);
-        for (int i = 0; i < n; ++i) X[i + (size_t)k * n] = E[i + (size_t)k * n] * s;
-        V[k + (size_t)k * R] = 1.0;
+        for (int i = 0; i < n; ++i) X0[i + (size_t)k * n] = E[i + (size_t)k * n] * s;
     }
+    // The right singular vectors of X come from the one-sided Jacobi below; for tall X it
+    // runs on the R x R triangle of a QR factorisation (same right singular vectors).
+    const bool tall = n > R;
+    const int m = tall ? R : n;
+    std::vector<double> X = tall ? householder_r(X0, n, R) : X0;
+    std::vector<double> V((size_t)R * R, 0.0), nrm(R);
+    for (int k = 0; k < R; ++k) V[k + (size_t)k * R] = 1.0;
+    const int n_full = n;
+    n = m;
     auto dot = [&](int p, int q) {
         double s = 0.0;
         const double* a = &X[(size_t)p * n];
@@ -344,11 +381,16 @@ bool compress_factor(const double* E, int n, int R, const double* xa, double tol
     int r = 0;
     while (r < R && std::sqrt(nrm[idx[r]]) > tol * smax) ++r;
     out.r = r;
-    out.Et.assign((size_t)n * r, 0.0);
+    out.Et.assign((size_t)n_full * r, 0.0);
     out.Mt.assign((size_t)r * R, 0.0);
     for (int a = 0; a < r; ++a) {
         const int k = idx[a];
-        for (int i = 0; i < n; ++i) out.Et[i + (size_t)a * n] = X[i + (size_t)k * n];
+        // Et[:, a] = X0 V[:, k] (= U S column; computed from the full matrix)
+        for (int i = 0; i < n_full; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < R; ++j) s += X0[i + (size_t)j * n_full] * V[j + (size_t)k * R];
+            out.Et[i + (size_t)a * n_full] = s;
+        }
         for (int j = 0; j < R; ++j)
             out.Mt[a + (size_t)j * r] = (xa[j] != 0.0) ? V[j + (size_t)k * R] / std::fabs(xa[j]) : 0.0;
     }

@@ -1,0 +1,111 @@
+"""Edge cases of the C ABI on the GPU: empty and zero inputs, degenerate grid sizes, error
+codes, and a large grid (n = 1023, 1.07e9 points) checked at sampled points against the
+closed-form solution for grid sine modes (eigenvectors of A, Section 3.2)."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import fc_inputs as fi
+from oracle import cp, full
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import paper_1809_01971_gb300 as m
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def test_empty_and_zero_inputs(fc):
+    n, d = 20, 3
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, 1e-8)
+    empty = fc.CP(d, n, 4)
+    Y = fc.CP(d, n, h.info.rank_symbol * 4)
+    fc.fc_apply(h, empty, Y)
+    assert Y.rank == 0
+    T = fc.CP(d, n, 32)
+    fc.fc_apply_trunc(h, 0, empty, 1e-8, 32, T)
+    assert T.rank == 0
+    fc.fc_truncate(h, empty, 1e-8, 32, T)
+    assert T.rank == 0
+    U = fc.CP(d, n, 32)
+    info = fc.fc_solve(h, empty, U)
+    assert info.status == 0 and info.iters == 0 and U.rank == 0
+    zero = fc.CP.from_factors(np.zeros(1), [np.ones((n, 1))] * d)
+    info = fc.fc_solve(h, zero, U)
+    assert info.status == 0 and U.rank == 0
+    assert fc.fc_inner(h, zero, zero) == 0.0
+
+
+@pytest.mark.parametrize("n,d", [(1, 2), (2, 2), (1, 3), (2, 3), (3, 3)])
+def test_degenerate_grid_sizes(fc, n, d):
+    """n = 1, 2, 3 interior points: the CP solve still equals the full-format solution."""
+    X = fi.random_cp(n, d, 2, seed=40 + n)
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, 1e-10)
+    U = fc.CP(d, n, 32)
+    info = fc.fc_solve(h, fc.CP.from_factors(*X), U, tol=1e-10, eps=1e-10)
+    ref = full.solve_full(cp.to_full(X), 0.5, 1.0, 1e-2)
+    e = rel(fc.fc_to_full(h, U).cpu().numpy(), ref)
+    print(f"n={n} d={d}: iters {info.iters} rank {U.rank} err {e:.2e}")
+    assert info.status == 0 and e < 1e-8
+
+
+def test_error_codes(fc):
+    n, d = 16, 3
+    h = fc.fc_setup(n, d, 0.5, 1.0, 1e-2, 1e-8)
+    X = fc.CP.from_factors(*fi.random_cp(n, d, 3, seed=50))
+    small = fc.CP(d, n, 5)
+    with pytest.raises(fc.FCError) as ex:
+        fc.fc_apply(h, X, small)
+    assert ex.value.code == fc.fc.FC_ERANK and small.rank == h.info.rank_symbol * 3
+    with pytest.raises(fc.FCError) as ex:
+        fc.fc_solve(h, X, fc.CP(d, n, 4))                  # u.cap below the rank cap
+    assert ex.value.code == fc.fc.FC_ERANK
+    # a handle without workspace
+    L = fc.lib()
+    raw = ctypes.c_void_p()
+    assert L.fc_setup(n, d, 0.5, 1.0, 1e-2, 1e-8, None, ctypes.byref(raw)) == 0
+    out = fc.CP(d, n, 200)
+    cx, co = X.desc(), out.desc()
+    assert L.fc_apply(raw, ctypes.byref(cx), ctypes.byref(co), None) == fc.fc.FC_EWORKSPACE
+    L.fc_destroy(raw)
+    # mismatched descriptor
+    other = fc.CP.from_factors(*fi.random_cp(n + 1, d, 2, seed=51))
+    with pytest.raises(fc.FCError) as ex:
+        fc.fc_inner(h, X, other)
+    assert ex.value.code == fc.fc.FC_EINVAL
+
+
+def test_large_grid_sine_modes_n1023(fc):
+    """n = 1023 (1.07e9 grid points): a rank-2 right-hand side of grid sine modes, exact
+    solution sum_m c_m b_m / g(rho_m); compared at 400 sampled grid points."""
+    n, d, alpha, gamma_ = 1023, 3, 0.5, 1e-3
+    modes = [((1, 2, 3), 1.0), ((3, 1, 2), -0.5)]
+    y = fi.concat_cp(*[fi.sine_cp(n, m) for m, _ in modes])
+    y = (np.array([c for _, c in modes]), y[1])
+    h = fc.fc_setup(n, d, alpha, 1.0, gamma_, 1e-10)
+    U = fc.CP(d, n, 32)
+    info = fc.fc_solve(h, fc.CP.from_factors(*y), U, tol=1e-10, eps=1e-10)
+    xi, Uf = U.factors()
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, n, size=(400, d))
+    got = np.array([np.sum(xi * np.prod([Uf[l][i[l], :] for l in range(d)], axis=0)) for i in idx])
+    N = n + 1
+    x = fi.grid(n)
+    ref = np.zeros(len(idx))
+    for (m, c) in modes:
+        rho = sum((2 * N) ** 2 * math.sin(math.pi * mm / (2 * N)) ** 2 for mm in m)
+        g = rho ** (-alpha) + gamma_ * rho ** alpha
+        ref += c / g * np.prod([np.sin(math.pi * m[l] * x[idx[:, l]]) for l in range(d)], axis=0)
+    e = rel(got, ref)
+    print(f"n=1023 sine modes: iters {info.iters} rank {U.rank} sampled err {e:.2e}")
+    assert info.status == 0 and e < 1e-8
