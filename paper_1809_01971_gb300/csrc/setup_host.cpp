@@ -249,6 +249,15 @@ bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, do
     out.rho_min = rmin;
     out.rho_max = rmax;
     if (rank < 1) return false;
+    if (!(rmax > rmin * (1.0 + 1e-9))) {
+        // a single eigenvalue (n = 1): the exact inverse symbol is the constant 1/g(rho_min)
+        out.tau.push_back(0.0);
+        out.w.push_back(1.0 / g_exact(rmin, alpha, beta, gamma));
+        out.mode.push_back(-1);
+        out.r_minus = 1;
+        out.err = 0.0;
+        return true;
+    }
     const int G = 3000;
     std::vector<double> tau(rank), rho(G), g(G);
     const double lt0 = std::log(0.2 / rmax), lt1 = std::log(20.0 / rmin);
