@@ -6,10 +6,9 @@
 namespace fc {
 
 // ---- k_linalg.cu ---------------------------------------------------------------------
-size_t jacobi_smem(int cmax);
 size_t pchol_smem();
 // ---- k_symeig.cu ------------------------------------------------------------------------
-// Same contract as launch_jacobi: item b is the symmetric c x c matrix at A + b*bsA with
+// Batched symmetric eigen-decomposition: item b is the symmetric c x c matrix at A + b*bsA with
 // c = dims ? min(dims[b*dstride], cmax) : cmax; eigenvalues descending into ev + b*bsE,
 // orthonormal eigenvectors as columns of V + b*bsV (cmax x cmax, zero-padded).
 void launch_symeig(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
@@ -26,9 +25,6 @@ size_t gjacobi_smem();
 cudaError_t set_symeig_attributes();
 // Opt the large-shared-memory kernels in to their dynamic shared memory (per device).
 cudaError_t set_linalg_attributes();
-void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
-                   const int* dims, int dstride, int cmax, double* ev, long long bsE,
-                   double* V, int ldv, long long bsV);
 void launch_pchol(cudaStream_t st, int batch, const double* M, int ldm, long long bsM,
                   const int* dims, int dstride, int cmax, double relTol, double* T, int ldt,
                   long long bsT, int* rank, int rstride);
@@ -67,17 +63,13 @@ void launch_sketch_kr(cudaStream_t st, int d, int n, int Ra, int S, int c, const
                       int lde, long long bsE, const double* xa, const double* Yh, int ldy,
                       long long bsY, const double* xb, unsigned long long seed, double* Y,
                       int ldo, long long bsO, double* tmp);
-void launch_weighted_energy(cudaStream_t st, int d, int n, int K, const double* U, int ldu,
-                            long long bsU, const double* w, double* tr);
 // Yr = Y - Q P (deflation), then columns of Yr scaled to unit norm (zero if tiny)
 void launch_deflate_normalize(cudaStream_t st, int d, int n, int c, double* Yr, int ld,
                               long long bs, const double* Yorig, double relTiny);
 // Q[:, off + j] = Qr[:, j] for j < min(cr, c - off), off = c1 (device counts per mode)
 void launch_combine_cols(cudaStream_t st, int d, int n, int c, double* Q, int ld, long long bs,
                          const double* Qr, const int* c1, const int* cr, int* ctot);
-// per-mode energy: KR: sum_i GE[i,i] * GY[i,i];  dense: sum_k w_k^2 (all modes equal)
-void launch_trace_kr(cudaStream_t st, int d, int n, const double* GE, int lde, long long bsE,
-                     const double* GY, int ldy, long long bsY, double* tr);
+// out[0..nout) = sum_k w_k^2
 void launch_sumsq(cudaStream_t st, int K, const double* w, double* out, int nout);
 // out[l] = scale * sum_{e < count} p[l*stride + e]^2
 void launch_block_energy(cudaStream_t st, int d, long long count, const double* p,
@@ -106,7 +98,6 @@ void launch_to_full(cudaStream_t st, int d, int n, int R, const double* xi, cons
 // u_hat[i] /= g(rho_i) (full-format eigenbasis solve)
 void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double alpha,
                        double beta, double gamma, double* x);
-void launch_fill(cudaStream_t st, double* p, size_t count, double v);
 void launch_copy_weights(cudaStream_t st, int K, const double* src, double scale, double* dst);
 // w[(k,j)] = xa[k] * xb[j]
 void launch_outer_weights(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,

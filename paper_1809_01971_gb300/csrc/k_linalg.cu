@@ -1,6 +1,4 @@
-// Small dense FP64 linear algebra on one CTA per problem (sizes <= kMaxC = 64):
-//   * cyclic two-sided Jacobi eigen-decomposition of symmetric matrices (the SVDs of the
-//     RHOSVD truncation, Section 5, are taken through the eigen-decomposition of Grams),
+// Small dense FP64 linear algebra on one CTA (or warp) per problem (sizes <= kMaxC = 64):
 //   * pivoted Cholesky orthonormaliser (range of a sketch, Gram-Schmidt by Cholesky),
 //   * rank selection by the Frobenius tail rule and canonical-term selection.
 #include "fc_common.cuh"
@@ -8,159 +6,6 @@
 #include <math.h>
 
 namespace fc {
-
-// ---------------------------------------------------------------------------------------
-// Jacobi eigen-decomposition.  Item b: symmetric c x c matrix at A + b*bsA (ld lda),
-// c = dims ? min(dims[b*dstride], cmax) : cmax.  Writes eigenvalues in descending order to
-// ev + b*bsE (cmax entries, zero-padded) and the eigenvectors as columns of V + b*bsV
-// (ld ldv, cmax x cmax, zero-padded).  Rounds follow the circle (round-robin) ordering so
-// the m/2 rotations of a round are disjoint and are applied together.
-// ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-jacobi_eig_kernel(const double* __restrict__ A, int lda, long long bsA,
-                  const int* __restrict__ dims, int dstride, int cmax,
-                  double* __restrict__ ev, long long bsE,
-                  double* __restrict__ V, int ldv, long long bsV, int maxSweeps, int prof)
-{
-    extern __shared__ double sm[];
-    const int b = blockIdx.x;
-    int c = cmax;
-    if (dims) c = min(dims[b * dstride], cmax);
-    if (c < 0) c = 0;
-    (void)prof;
-    const int m = (c + 1) & ~1;           // even number of players
-    const int S = m + 1;                  // smem row stride
-    double* a = sm;                       // m x S
-    double* v = a + m * S;                // m x S
-    double* coefS = v + m * S;            // self coefficient per index
-    double* coefP = coefS + m;            // partner coefficient per index
-    int* partner = (int*)(coefP + m);
-    int* rotated = partner + m;           // per pair: rotation applied
-    __shared__ double red[32];
-    __shared__ int anyRot;
-
-    const double* Ab = A + b * bsA;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e % m, j = e / m;
-        a[i * S + j] = (i < c && j < c) ? Ab[i + (long long)j * lda] : 0.0;
-        v[i * S + j] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    double fro = 0.0;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        double x = a[(e % m) * S + e / m];
-        fro += x * x;
-    }
-    fro = sqrt(block_sum(fro, red));
-    const double absTol = 1e-18 * fro;
-    const int half = m / 2;
-
-    for (int sweep = 0; sweep < maxSweeps && m >= 2; ++sweep) {
-        if (threadIdx.x == 0) anyRot = 0;
-        __syncthreads();
-        for (int rnd = 0; rnd < m - 1; ++rnd) {
-            // rotation parameters, one thread per disjoint pair
-            for (int i = threadIdx.x; i < half; i += blockDim.x) {
-                int p, q;
-                if (i == 0) { p = rnd; q = m - 1; }
-                else { p = (rnd + i) % (m - 1); q = (rnd - i + (m - 1)) % (m - 1); }
-                if (p > q) { int t = p; p = q; q = t; }
-                double app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
-                double cs = 1.0, sn = 0.0;
-                int rot = 0;
-                double thr = fmax(2.2e-16 * sqrt(fabs(app * aqq)), absTol);
-                if (fabs(apq) > thr) {
-                    double th = (aqq - app) / (2.0 * apq);
-                    double t;
-                    if (fabs(th) > 1e150) t = 0.5 / th;
-                    else t = copysign(1.0, th) / (fabs(th) + sqrt(th * th + 1.0));
-                    cs = 1.0 / sqrt(t * t + 1.0);
-                    sn = t * cs;
-                    rot = 1;
-                }
-                partner[p] = q; partner[q] = p;
-                coefS[p] = cs; coefP[p] = -sn;
-                coefS[q] = cs; coefP[q] = sn;
-                rotated[i] = rot;
-                if (rot) anyRot = 1;
-            }
-            __syncthreads();
-            // A <- J^T A J on 2x2 blocks (pair I) x (pair J); in place, each block owned
-            // by one thread.  Pair index of player x: position in the round (recomputed).
-            for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
-                int pi = e % half, pj = e / half;
-                int p1, q1, p2, q2;
-                if (pi == 0) { p1 = rnd; q1 = m - 1; } else { p1 = (rnd + pi) % (m - 1); q1 = (rnd - pi + (m - 1)) % (m - 1); }
-                if (pj == 0) { p2 = rnd; q2 = m - 1; } else { p2 = (rnd + pj) % (m - 1); q2 = (rnd - pj + (m - 1)) % (m - 1); }
-                if (!rotated[pi] && !rotated[pj]) continue;
-                int xs[2] = {p1, q1}, ys[2] = {p2, q2};
-                double o[2][2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        int x = xs[u], y = ys[w];
-                        int xp = partner[x], yp = partner[y];
-                        double cx = coefS[x], sx = coefP[x], cy = coefS[y], sy = coefP[y];
-                        o[u][w] = cx * (cy * a[x * S + y] + sy * a[x * S + yp]) +
-                                  sx * (cy * a[xp * S + y] + sy * a[xp * S + yp]);
-                    }
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) a[xs[u] * S + ys[w]] = o[u][w];
-                if (pi == pj && rotated[pi]) {   // annihilated entry: exact zero
-                    a[xs[0] * S + xs[1]] = 0.0;
-                    a[xs[1] * S + xs[0]] = 0.0;
-                }
-            }
-            // V <- V J: rows of V stored as v[row*S + col]
-            for (int e = threadIdx.x; e < m * half; e += blockDim.x) {
-                int r = e % m, pi = e / m;
-                if (!rotated[pi]) continue;
-                int p, q;
-                if (pi == 0) { p = rnd; q = m - 1; } else { p = (rnd + pi) % (m - 1); q = (rnd - pi + (m - 1)) % (m - 1); }
-                double vp = v[r * S + p], vq = v[r * S + q];
-                v[r * S + p] = coefS[p] * vp + coefP[p] * vq;
-                v[r * S + q] = coefS[q] * vq + coefP[q] * vp;
-            }
-            __syncthreads();
-        }
-        if (!anyRot) break;
-        __syncthreads();
-    }
-    // sort descending (rank by counting; ties by index), write padded outputs
-    double* evb = ev + b * bsE;
-    double* Vb = V + b * bsV;
-    for (int e = threadIdx.x; e < cmax * cmax; e += blockDim.x) Vb[(e % cmax) + (long long)(e / cmax) * ldv] = 0.0;
-    for (int i = threadIdx.x; i < cmax; i += blockDim.x) evb[i] = 0.0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < c; i += blockDim.x) {
-        double di = a[i * S + i];
-        int rk = 0;
-        for (int j = 0; j < c; ++j) {
-            double dj = a[j * S + j];
-            rk += (dj > di) || (dj == di && j < i);
-        }
-        evb[rk] = di;
-        for (int r = 0; r < c; ++r) Vb[r + (long long)rk * ldv] = v[r * S + i];
-    }
-}
-
-size_t jacobi_smem(int cmax) {
-    int m = (cmax + 1) & ~1;
-    return sizeof(double) * (2 * (size_t)m * (m + 1) + 2 * m) + sizeof(int) * 2 * m;
-}
-
-void launch_jacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
-                   const int* dims, int dstride, int cmax, double* ev, long long bsE,
-                   double* V, int ldv, long long bsV)
-{
-    if (batch <= 0) return;
-    size_t sm = jacobi_smem(cmax);
-    note_launch(); jacobi_eig_kernel<<<batch, 256, sm, st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv,
-                                               bsV, 30, 0);
-}
 
 // ---------------------------------------------------------------------------------------
 // Pivoted-Cholesky orthonormaliser.  Item b: Gram M = Y^T Y (c x c, ld ldm) of a sketch Y.
@@ -265,10 +110,6 @@ size_t pchol_smem() { return sizeof(double) * 3 * kMaxC * (kMaxC + 1); }
 
 cudaError_t set_linalg_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)jacobi_smem(kMaxC));
-    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pchol_smem());
 }

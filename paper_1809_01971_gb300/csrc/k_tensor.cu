@@ -205,28 +205,6 @@ void launch_sketch_kr(cudaStream_t st, int d, int n, int Ra, int S, int c, const
     note_launch(); hadamard_kernel<<<dim3(blocks, d), 256, 0, st>>>(cnt, n, c, Y, ldo, bsO, tmp, ldo, bsO);
 }
 
-// tr[l] = sum_k w_k^2 ||U_l[:, k]||^2  (Frobenius energy of the weighted side matrix)
-__global__ void weighted_energy_kernel(int n, int K, const double* U, int ldu, long long bsU,
-                                       const double* w, double* tr)
-{
-    __shared__ double red[32];
-    const int l = blockIdx.x;
-    double s = 0.0;
-    for (long long e = threadIdx.x; e < (long long)n * K; e += blockDim.x) {
-        int i = (int)(e % n), k = (int)(e / n);
-        double v = U[l * bsU + i + (long long)k * ldu] * w[k];
-        s += v * v;
-    }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) tr[l] = s;
-}
-
-void launch_weighted_energy(cudaStream_t st, int d, int n, int K, const double* U, int ldu,
-                            long long bsU, const double* w, double* tr)
-{
-    note_launch(); weighted_energy_kernel<<<d, 1024, 0, st>>>(n, K, U, ldu, bsU, w, tr);
-}
-
 // Yr (already Y - Q1 P) columns normalised to unit length, relative to the original column
 // norms: a column whose remainder is below relTiny * ||Y[:, t]|| is zeroed.
 __global__ void deflate_normalize_kernel(int n, double* Yr, int ld, long long bs,
@@ -275,24 +253,6 @@ void launch_combine_cols(cudaStream_t st, int d, int n, int c, double* Q, int ld
     int blocks = (int)((cnt + 255) / 256);
     if (blocks > 1024) blocks = 1024;
     note_launch(); combine_cols_kernel<<<dim3(blocks, d), 256, 0, st>>>(n, c, Q, ld, bs, Qr, c1, cr, ctot);
-}
-
-__global__ void trace_kr_kernel(int n, const double* GE, int lde, long long bsE, const double* GY,
-                                int ldy, long long bsY, double* tr)
-{
-    __shared__ double red[32];
-    const int l = blockIdx.x;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        s += GE[l * bsE + i + (long long)i * lde] * GY[l * bsY + i + (long long)i * ldy];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) tr[l] = s;
-}
-
-void launch_trace_kr(cudaStream_t st, int d, int n, const double* GE, int lde, long long bsE,
-                     const double* GY, int ldy, long long bsY, double* tr)
-{
-    note_launch(); trace_kr_kernel<<<d, 256, 0, st>>>(n, GE, lde, bsE, GY, ldy, bsY, tr);
 }
 
 __global__ void sumsq_kernel(int K, const double* w, double* out, int nout)
@@ -519,21 +479,6 @@ void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double 
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 152 * 64) blocks = 152 * 64;
     note_launch(); full_scale_kernel<<<blocks, 256, 0, st>>>(d, n, lam, alpha, beta, gamma, x);
-}
-
-__global__ void fill_kernel(double* p, size_t count, double v)
-{
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
-         e += (size_t)gridDim.x * blockDim.x)
-        p[e] = v;
-}
-
-void launch_fill(cudaStream_t st, double* p, size_t count, double v)
-{
-    if (count == 0) return;
-    int blocks = (int)((count + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
-    note_launch(); fill_kernel<<<blocks, 256, 0, st>>>(p, count, v);
 }
 
 __global__ void copy_weights_kernel(int K, const double* src, double scale, double* dst)
