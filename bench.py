@@ -9,13 +9,19 @@ preconditioner CP factors, workspace) is done once before timing, as a library u
 would for repeated solves with one operator; the timed step is the full Algorithm 1
 (PCG with RHOSVD truncation) for all six right-hand sides.
 
+The step runs in each of the three contraction forms of the library (fc_setup precision
+0: FP64; 1: double-float FP32; 2: FP64-accurate digit products on the BF16 tensor cores);
+`forms` reports all three, and `value` is the fastest form whose solutions are all within
+1e-6 of the exact one (`config.form`), `vs_plain_fp64` its ratio to the FP64 form.
+
 `value`  : device-resident solves/s (CUDA events on the launching stream, L2 flushed
            between steps with a 512 MiB write, outside the events).
-`e2e`    : the same through the public API with host buffers: every step copies the
-           right-hand sides from pinned host memory and reads the solutions back.
+`e2e`    : the same through the public API with host buffers, in the reported form: every
+           step copies the right-hand sides from pinned host memory and reads the
+           solutions back.
 Accuracy : after timing, every solution is compared with the library's full-format
            FP64 eigenbasis solve (16.6M points), and the largest relative L2 error is
-           reported; a run whose error exceeds 1e-6 exits non-zero.
+           reported; a run where any form's error exceeds 1e-6 exits non-zero.
 `--impl reference` times the CPU FP64 oracle on the same workload (one problem per
 step, cycling) on this host's cores.
 """
@@ -33,7 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "3D control solves/s at rel-err<=1e-6 (plain FP64, CP-PCG)"
+METRIC = "3D control solves/s at rel-err<=1e-6 (CP-PCG, batched; fastest contraction form meeting the bound, vs plain FP64)"
 UNIT = "solves/s"
 WORKLOAD = "3d_n255_6problems_alpha{0.25,0.5,0.75}_gamma{1e-1,1e-3}_rank5rhs_tol1e-8_eps1e-9_cap192"
 L2_FLUSH_BYTES = 512 << 20
@@ -176,6 +182,13 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 EIG_TRAFFIC_BYTES = None
 
 
+FORMS = {0: ("fp64", "f64", "FP64 throughout"),
+         1: ("df32", "f32x2", "large contractions in double-float FP32 (hi+lo); rest FP64"),
+         2: ("tc64", "bf16-digits/f64", "large contractions as exact products of 8 fixed-point "
+                                        "7-bit digits on the BF16 tensor cores (tcgen05, FP32 "
+                                        "TMEM accumulation, FP64-level error); rest FP64")}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -196,24 +209,11 @@ def main():
     main_stream = torch.cuda.current_stream()
     probs = problems(args.problems)
     # independent problems: each rank solves the full six-problem set (weak scaling)
-    hs, Bs, Us = [], [], []
-    for p in probs:
-        h = fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank)
-        hs.append(h)
-        Bs.append(fc.CP.from_factors(*p.rhs(), device=dev))
-        Us.append(fc.CP(p.d, p.n, p.max_rank, device=dev))
+    Bs = [fc.CP.from_factors(*p.rhs(), device=dev) for p in probs]
     streams = [torch.cuda.Stream(device=dev) for _ in probs]
     tols = [p.tol for p in probs]
     epss = [p.eps for p in probs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def step():
-        # the step's problems run concurrently, one stream each (fc_solve_batched)
-        return fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss)
-
-    def step_sequential():
-        return [fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=main_stream)
-                for p, h, B, U in zip(probs, hs, Bs, Us)]
 
     def timed(fn):
         """Device time of fn() from CUDA events: start on the main stream, every problem
@@ -231,58 +231,86 @@ def main():
         e1.synchronize()
         return e0.elapsed_time(e1), out
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    # accuracy reference: the library's full-format FP64 eigenbasis solve of every problem
+    nn = probs[0].n ** 3
+    full_b = torch.empty(nn, dtype=torch.float64, device=dev)
+    tmp = torch.empty_like(full_b)
+    full_u = []
+    href = [fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank)
+            for p in probs]
+    for p, h, B in zip(probs, href, Bs):
+        fc.fc_to_full(h, B, out=full_b)          # column-major n^3
+        u = torch.empty_like(full_b)
+        fc.fc_full_solve(h, full_b, u, tmp)
+        full_u.append(u)
+
     sampler = ClockSampler(local)
     sampler.start()
-    times, iters = [], []
-    barrier()
-    fc.fc_prof_enable(fc.fc.PROF_JACOBI)
-    launches0 = fc.fc_launch_count()
-    for _ in range(args.steps):
-        ms, infos = timed(step)
-        times.append(ms)
-        iters.append([i.iters for i in infos])
-    launches = fc.fc_launch_count() - launches0
-    jac_n, jac_ms, jac_work = fc.fc_prof_read()
-    barrier()
-    clocks = sampler.stop()
-    t_total = sum(times) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
-    solves = len(probs) * args.steps * world
-    value = solves / t_total
+    results = {}
+    for form in (0, 1, 2):
+        hs = href if form == 0 else [
+            fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank,
+                        precision=form) for p in probs]
+        Us = [fc.CP(p.d, p.n, p.max_rank, device=dev) for p in probs]
 
-    # the same problems one after another on one stream (context for the batched number)
+        def step(hs=hs, Us=Us):
+            # the step's problems run concurrently, one stream each (fc_solve_batched)
+            return fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss)
+
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        fc.fc_prof_enable(fc.fc.PROF_JACOBI)
+        launches0 = fc.fc_launch_count()
+        times, iters = [], []
+        for _ in range(args.steps):
+            ms, infos = timed(step)
+            times.append(ms)
+            iters.append([i.iters for i in infos])
+        launches = fc.fc_launch_count() - launches0
+        prof = fc.fc_prof_read()
+        barrier()
+        t_total = max_over_ranks(sum(times) / 1e3)
+        err = 0.0
+        for h, U, u in zip(hs, Us, full_u):
+            fc.fc_to_full(h, U, out=tmp)
+            err = max(err, float(torch.linalg.norm(tmp - u) / torch.linalg.norm(u)))
+        results[form] = {"hs": hs, "Us": Us, "step": step, "t_total": t_total,
+                         "value": len(probs) * args.steps * world / t_total,
+                         "launches": launches, "prof": prof, "iters": iters[-1], "err": err}
+    clocks = sampler.stop()
+
+    ok = [f for f in results if results[f]["err"] <= args.max_err]
+    best = max(ok, key=lambda f: results[f]["value"]) if ok else 0
+    R = results[best]
+    value, t_total = R["value"], R["t_total"]
+    solves = len(probs) * args.steps * world
+
+    # the FP64 problems one after another on one stream (context for the batched number)
+    hs0, Us0 = results[0]["hs"], results[0]["Us"]
+
+    def step_sequential():
+        return [fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=main_stream)
+                for p, h, B, U in zip(probs, hs0, Bs, Us0)]
+
     seq_steps = max(1, args.steps // 2)
     seq_ms = sum(timed(step_sequential)[0] for _ in range(seq_steps))
     seq_value = len(probs) * seq_steps / (seq_ms / 1e3)
 
-    # precision form: the same batched step with the large contractions in double-float FP32
-    # arithmetic (fc_setup precision=1), its own handles; accuracy checked below as well
-    hs_df = [fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank,
-                         precision=1) for p in probs]
-    Us_df = [fc.CP(p.d, p.n, p.max_rank, device=dev) for p in probs]
-
-    def step_df():
-        return fc.fc_solve_batched(hs_df, Bs, Us_df, streams, tol=tols, eps=epss)
-
-    for _ in range(args.warmup):
-        step_df()
-    torch.cuda.synchronize()
-    df_ms = sum(timed(step_df)[0] for _ in range(args.steps))
-    df_value = len(probs) * args.steps / (df_ms / 1e3)
-
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers, in the reported form
+    hsb, Usb = R["hs"], R["Us"]
     host_in = []
     for p in probs:
         xi, U = p.rhs()
@@ -295,13 +323,13 @@ def main():
 
     def e2e_step():
         for (xi_h, U_h), p, B, s_ in zip(host_in, probs, Bs, streams):
-            R = xi_h.numel()
+            R_ = xi_h.numel()
             with torch.cuda.stream(s_):
-                B.xi[:R].copy_(xi_h, non_blocking=True)
-                B.U[:, :R, :p.n].copy_(U_h, non_blocking=True)
-            B.rank = R
-        fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss)
-        for (xo, Uo), p, U, s_ in zip(host_out, probs, Us, streams):
+                B.xi[:R_].copy_(xi_h, non_blocking=True)
+                B.U[:, :R_, :p.n].copy_(U_h, non_blocking=True)
+            B.rank = R_
+        fc.fc_solve_batched(hsb, Bs, Usb, streams, tol=tols, eps=epss)
+        for (xo, Uo), p, U, s_ in zip(host_out, probs, Usb, streams):
             with torch.cuda.stream(s_):
                 xo.copy_(U.xi[:p.max_rank], non_blocking=True)
                 Uo.copy_(U.U[:, :p.max_rank, :p.n], non_blocking=True)
@@ -312,30 +340,10 @@ def main():
     for _ in range(args.steps):
         e2e_times.append(timed(e2e_step)[0])
     barrier()
-    e2e_t = sum(e2e_times) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_t], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = solves / e2e_t
+    e2e_value = solves / max_over_ranks(sum(e2e_times) / 1e3)
 
-    # accuracy against the library's full-format FP64 eigenbasis solve
-    max_err = 0.0
-    nn = probs[0].n ** 3
-    full_b = torch.empty(nn, dtype=torch.float64, device=dev)
-    full_u = torch.empty_like(full_b)
-    tmp = torch.empty_like(full_b)
-    max_err_df = 0.0
-    for p, h, B, U, Udf in zip(probs, hs, Bs, Us, Us_df):
-        fc.fc_to_full(h, B, out=full_b)          # column-major n^3 in full_b
-        fc.fc_full_solve(h, full_b, full_u, tmp)
-        fc.fc_to_full(h, U, out=tmp)
-        err = float(torch.linalg.norm(tmp - full_u) / torch.linalg.norm(full_u))
-        max_err = max(max_err, err)
-        fc.fc_to_full(h, Udf, out=tmp)
-        err = float(torch.linalg.norm(tmp - full_u) / torch.linalg.norm(full_u))
-        max_err_df = max(max_err_df, err)
     roofline = None
+    jac_n, jac_ms, jac_work = R["prof"]
     if jac_n > 0 and jac_ms > 0:
         achieved = jac_work / jac_n / (jac_ms / jac_n * 1e-3) / 1e12     # TFLOP/s
         peak = FP64_PEAK_GFLOPS / 1e3
@@ -349,24 +357,30 @@ def main():
                     "event_ms_over_step_ms": jac_ms / (t_total * 1e3),
                     "note": "launches overlap across the problem streams, so summed event time can exceed step time"}
     if rank == 0:
+        name, dtype, what = FORMS[best]
+        forms = {FORMS[f][0]: {"value": results[f]["value"], "unit": UNIT,
+                               "ms_per_step": 1e3 * results[f]["t_total"] / args.steps,
+                               "max_rel_err_vs_full": results[f]["err"],
+                               "pcg_iters": results[f]["iters"],
+                               "gpu_launches": int(results[f]["launches"]),
+                               "contractions": FORMS[f][2]} for f in results}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": WORKLOAD, "problems_per_step": len(probs),
+                           "form": name,
                            "l2": "flushed between steps (512 MiB write, untimed)",
                            "setup": "per operator, before timing",
                            "concurrency": "fc_solve_batched: one stream and host thread per problem",
-                           "pcg_iters": iters[-1]},
-                "sequential_value": seq_value,
-                "precision_form": {"value": df_value, "unit": UNIT,
-                                   "ms_per_step": df_ms / args.steps,
-                                   "max_rel_err_vs_full": max_err_df,
-                                   "contractions": "double-float FP32 (hi+lo), rest FP64"},
-                "max_rel_err_vs_full": max_err,
+                           "pcg_iters": R["iters"]},
+                "forms": forms,
+                "vs_plain_fp64": value / results[0]["value"],
+                "sequential_fp64_value": seq_value,
+                "max_rel_err_vs_full": R["err"],
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": int(launches),
+                "gpu_launches": int(R["launches"]),
                 "clocks": clocks,
                 "roofline": roofline,
                 "cpu_baseline": None}
@@ -375,7 +389,7 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-    return 0 if max(max_err, max_err_df) <= args.max_err else 3
+    return 0 if all(results[f]["err"] <= args.max_err for f in results) else 3
 
 
 if __name__ == "__main__":

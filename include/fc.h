@@ -46,7 +46,9 @@ enum {
     FC_ENAN = -5,         /* non-finite scalar in the recurrences                          */
     FC_ECUDA = -6,        /* CUDA runtime error (message via fc_last_cuda_error)           */
     FC_EWORKSPACE = -7,   /* no workspace bound, or bound workspace too small              */
-    FC_ESETUP = -8        /* quadrature / preconditioner construction failed               */
+    FC_ESETUP = -8,       /* quadrature / preconditioner construction failed               */
+    FC_ETIMEOUT = -9      /* a bounded wait inside a kernel expired (the kernel freed its  */
+                          /* resources and returned; results of the call are undefined)     */
 };
 
 typedef struct fc_ctx* fc_handle;
@@ -75,7 +77,11 @@ typedef struct fc_setup_opts {
     int precision;      /* 0: FP64 contractions; 1: the large contractions (DST, Khatri-Rao  */
                         /* projections, Tucker core) in double-float arithmetic on the FP32  */
                         /* pipe (hi + lo FP32 pairs, ~1e-14 relative), 64x GB300's FP64 rate; */
-                        /* eigen-solves, Grams of the sketch and scalars stay FP64 [0]        */
+                        /* 2: contractions of >= 2^24 multiply-adds on the BF16 tensor cores  */
+                        /* as exact products of 7-bit fixed-point digits of the FP64 operands */
+                        /* (8 digits, FP32-exact accumulation, error below FP64 rounding of  */
+                        /* the row/column scales).  Eigen-solves, sketch Grams and scalars   */
+                        /* stay FP64 in every form [0]                                        */
 } fc_setup_opts;
 
 typedef struct fc_setup_info {
@@ -235,6 +241,18 @@ unsigned long long fc_launch_count(void);
 int fc_symeig(int method, int batch, int m, const double* dev_A, int lda, long long strideA,
               double* dev_w, long long strideW, double* dev_V, int ldv, long long strideV,
               void* stream);
+
+/* C = alpha op(A) op(B) + beta C for column-major FP64 device matrices (op(A) M x K, op(B)
+ * K x N; op = transpose if transA / transB), in the given contraction form: 0 the FP64 tiled
+ * GEMM, 1 double-float on the FP32 pipe, 2 the BF16 tensor cores with 8 fixed-point digits
+ * per operand (any size; the solver routes only contractions of >= 2^24 multiply-adds
+ * there).  This is the contraction kernel of every form of the solver, exposed for testing
+ * and reuse: the paper has no counterpart of it.  All pointers are device pointers owned by
+ * the caller; lda >= rows of A as stored, etc.  Asynchronous on `stream`; FC_ETIMEOUT (form
+ * 2) only after a synchronisation of the stream inside the call.  Errors: FC_EINVAL. */
+int fc_dgemm(int precision, int transA, int transB, int M, int N, int K, double alpha,
+             const double* dev_A, int lda, const double* dev_B, int ldb, double beta,
+             double* dev_C, int ldc, void* stream);
 
 /* Kernel-class instrumentation.  fc_prof_enable(kclass) synchronises the device, clears the
  * counters and, until fc_prof_read, brackets every launch of that class with a pair of CUDA

@@ -5,8 +5,8 @@ Khoromskij, Schulz, arXiv:1809.01971).
 The compute path is libfc.so (CUDA kernels behind the C ABI of include/fc.h); this
 package holds its build script and the ctypes binding :mod:`.fc`.
 """
-from .fc import (CP, FCError, Handle, fc_apply, fc_apply_trunc, fc_full_solve, fc_get_symbol, fc_inner,
+from .fc import (CP, FCError, Handle, fc_apply, fc_apply_trunc, fc_dgemm, fc_full_solve, fc_get_symbol, fc_inner,
                  fc_inner_static, fc_launch_count, fc_prof_enable, fc_prof_read, fc_precond, fc_setup, fc_solve, fc_solve_batched, fc_state, fc_symeig, fc_to_full, fc_truncate, lib)
 
-__all__ = ["CP", "FCError", "Handle", "fc_apply", "fc_apply_trunc", "fc_full_solve", "fc_get_symbol", "fc_inner", "fc_inner_static", "fc_launch_count", "fc_prof_enable", "fc_prof_read",
+__all__ = ["CP", "FCError", "Handle", "fc_apply", "fc_apply_trunc", "fc_dgemm", "fc_full_solve", "fc_get_symbol", "fc_inner", "fc_inner_static", "fc_launch_count", "fc_prof_enable", "fc_prof_read",
            "fc_precond", "fc_setup", "fc_solve", "fc_solve_batched", "fc_state", "fc_symeig", "fc_to_full", "fc_truncate", "lib"]

@@ -310,6 +310,19 @@ struct KRIn {           // implicit Khatri-Rao tensor sum_{k,j} xa_k xb_j (x)_l 
 };
 struct DenseIn { const double* w; const double* U; int ld; long long bs; int K; };
 
+// The tensor-core GEMMs record an expired bounded wait in a device flag (fc_tc.cuh; one
+// flag for the process); calls of a handle in that form read and clear it after their
+// final stream synchronisation.
+int tc_status(const fc_ctx* h) {
+    if (h->prec != GP_TC64) return FC_OK;
+    int flag = 0;
+    CK(cudaMemcpyFromSymbol(&flag, g_tc_error, sizeof(int)));
+    if (!flag) return FC_OK;
+    const int zero = 0;
+    CK(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)));
+    return FC_ETIMEOUT;
+}
+
 // ---------------------------------------------------------------------------------------
 // Truncation (Section 5, RHOSVD canonical -> Tucker -> canonical).  Input either an
 // implicit Khatri-Rao tensor in the eigen-index domain (mat-vec outputs; the Tucker bases
@@ -454,13 +467,27 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     CKL();
     // ---- core: B3[(a + r0 b), c] = sum_K w_K C0[a,K] C1[b,K] C2[c,K] ----------------------
     const int RR = RM * RM;
-    LdCore A{w.C, w.C + RK, wK, CM, dims + D_R};
-    if (d == 3)
-        gemm_p(h->prec, st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, CM, 0}, 1.0, 0.0, w.core, RR, 0, 1,
-             dims + D_R12, dims + D_R3, nullptr);
-    else
-        gemm_p(h->prec, st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, w.core, RR, 0, 1, dims + D_R12, nullptr,
-             nullptr);
+    if (h->prec == GP_TC64) {
+        // tensor-core form: the weights are folded into the mode-1 factor first (C1 is not
+        // used after the core), so an operand element is a product of two factors, whose
+        // digits are formed from the exact mantissa product
+        launch_scale_cols(st, CM, (int)K, w.C + RK, CM, wK);
+        LdCoreW A{w.C, w.C + RK, CM, dims + D_R};
+        if (d == 3)
+            gemm_p(h->prec, st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, CM, 0}, 1.0, 0.0, w.core, RR, 0,
+                   1, dims + D_R12, dims + D_R3, nullptr);
+        else
+            gemm_p(h->prec, st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, w.core, RR, 0, 1, dims + D_R12,
+                   nullptr, nullptr);
+    } else {
+        LdCore A{w.C, w.C + RK, wK, CM, dims + D_R};
+        if (d == 3)
+            gemm_p(h->prec, st, RR, RM, (int)K, A, LdT{w.C + 2 * RK, CM, 0}, 1.0, 0.0, w.core, RR, 0,
+                   1, dims + D_R12, dims + D_R3, nullptr);
+        else
+            gemm_p(h->prec, st, RR, 1, (int)K, A, LdOnes{}, 1.0, 0.0, w.core, RR, 0, 1, dims + D_R12,
+                   nullptr, nullptr);
+    }
     CKL();
     launch_core_energy(st, d, w.core, RR, dims, w.scal + 12);
     // mode-3 rotation: G3 = B3^T B3, W3 = eigvecs, Srot = B3 W3
@@ -496,6 +523,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     CK(cudaMemcpyAsync(out.xi, w.sigma, sizeof(double) * maxq, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->hint, dims, sizeof(int) * D_SIZE, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (int rc_ = tc_status(h)) return rc_;
     out.rank = h->hint[D_Q];
     for (int l = 0; l < d; ++l) {
         h->stat_rsum += h->hint[D_R + l];
@@ -588,6 +616,7 @@ const char* fc_strerror(int code) {
         case FC_ECUDA: return "CUDA error";
         case FC_EWORKSPACE: return "workspace missing or too small";
         case FC_ESETUP: return "quadrature or preconditioner construction failed";
+        case FC_ETIMEOUT: return "a bounded wait inside a kernel expired (tensor-core pipeline)";
         default: return "unknown error";
     }
 }
@@ -610,6 +639,40 @@ int fc_symeig(int method, int batch, int m, const double* dev_A, int lda, long l
                        strideW, dev_V, ldv, strideV, true);
     CKL();
     return FC_OK;
+}
+
+int fc_dgemm(int precision, int transA, int transB, int M, int N, int K, double alpha,
+             const double* dev_A, int lda, const double* dev_B, int ldb, double beta,
+             double* dev_C, int ldc, void* stream) {
+    if (!(precision >= 0 && precision <= 2) || M < 0 || N < 0 || K < 0) return FC_EINVAL;
+    if (M == 0 || N == 0) return FC_OK;
+    if (!dev_C || ldc < M || (K > 0 && (!dev_A || !dev_B))) return FC_EINVAL;
+    if (lda < (transA ? K : M) || ldb < (transB ? N : K) || lda < 1 || ldb < 1) return FC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto run = [&](auto la, auto lb) -> int {
+        if (precision == 2) {
+            if (!gemm_tc(st, M, N, K, la, lb, alpha, beta, dev_C, ldc, 0, 1, nullptr, nullptr,
+                         nullptr))
+                return FC_ECUDA;
+            CKL();
+            CK(cudaStreamSynchronize(st));
+            int flag = 0;
+            CK(cudaMemcpyFromSymbol(&flag, g_tc_error, sizeof(int)));
+            if (flag) {
+                const int zero = 0;
+                CK(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)));
+                return FC_ETIMEOUT;
+            }
+            return FC_OK;
+        }
+        gemm_p(precision == 1 ? GP_DF32 : GP_F64, st, M, N, K, la, lb, alpha, beta, dev_C, ldc);
+        CKL();
+        return FC_OK;
+    };
+    if (!transA && !transB) return run(LdN{dev_A, lda, 0}, LdN{dev_B, ldb, 0});
+    if (!transA && transB) return run(LdN{dev_A, lda, 0}, LdT{dev_B, ldb, 0});
+    if (transA && !transB) return run(LdT{dev_A, lda, 0}, LdN{dev_B, ldb, 0});
+    return run(LdT{dev_A, lda, 0}, LdT{dev_B, ldb, 0});
 }
 
 int fc_prof_enable(int kclass) {
@@ -659,7 +722,7 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     fc_setup_opts opts{1e-10, 24, 32, 48, 0, 0, 0};
     if (o) {
         opts.directional = o->directional ? 1 : 0;
-        opts.precision = (o->precision == 1) ? 1 : 0;
+        opts.precision = (o->precision == 1 || o->precision == 2) ? o->precision : 0;
         if (o->delta_sym > 0) opts.delta_sym = o->delta_sym;
         if (o->precond_rank > 0) opts.precond_rank = o->precond_rank;
         if (o->max_rank > 0) opts.max_rank = o->max_rank;
@@ -686,7 +749,7 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     if (!h) return FC_EINVAL;
     h->n = n; h->d = d; h->alpha = alpha; h->beta = beta; h->gamma = gamma; h->eps = eps;
     h->alpha_eff = alpha_eff;
-    h->prec = opts.precision ? GP_DF32 : GP_F64;
+    h->prec = (opts.precision == 2) ? GP_TC64 : (opts.precision == 1) ? GP_DF32 : GP_F64;
     h->opts = opts;
     h->RA = (int)sym.tau.size();
     h->RS = sym.r_minus;
@@ -844,7 +907,7 @@ static int apply_common(fc_handle h, const fc_cp* x, fc_cp* y, void* stream, boo
     CKL();
     y->rank = (int)K;
     CK(cudaStreamSynchronize(st));
-    return FC_OK;
+    return tc_status(h);
 }
 
 int fc_apply(fc_handle h, const fc_cp* x, fc_cp* y, void* stream) {

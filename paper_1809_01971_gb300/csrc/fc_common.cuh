@@ -97,6 +97,14 @@ struct LdCore {
         return w[k] * C0[a + (long long)k * ldc] * C1[b + (long long)k * ldc];
     }
 };
+// A[(a + r0 b), k] = C0[a, k] C1w[b, k] with C1w = C1 diag(w) formed beforehand
+struct LdCoreW {
+    const double* C0; const double* C1w; int ldc; const int* r0p;
+    FC_DEV double operator()(int ab, int k, int) const {
+        int r0 = *r0p; int b = ab / r0, a = ab - b * r0;
+        return C0[a + (long long)k * ldc] * C1w[b + (long long)k * ldc];
+    }
+};
 // columns (k*S + b) of a column-major matrix, batch item b (the input column j of a
 // Khatri-Rao product): element (i, k) of batch b = p[i + (k*S + b)*ld]
 struct LdColsJ {
@@ -303,11 +311,19 @@ gemm_df_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
 __global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN, double beta,
                                      double* C, int ldc, long long bsC);
 
+}  // namespace fc
+#include "fc_tc.cuh"
+namespace fc {
+
 // Launch: the largest tile (64, 32, 16) whose grid still covers the 152 SMs, then split-K
 // until about 4 CTAs per SM (GB300 runs few FP64 FMAs per SM per clock, so the SM count
 // decides the rate).
-// Precision of a contraction: FP64, or double-float on the FP32 pipe (gemm_df_kernel).
-enum GemmPrec { GP_F64 = 0, GP_DF32 = 1 };
+// Precision of a contraction: FP64, double-float on the FP32 pipe (gemm_df_kernel), or
+// FP64-accurate digit products on the BF16 tensor cores (gemm_tc_kernel) for contractions
+// of at least kTcMinMacs multiply-adds (smaller ones stay on the FP64 kernel, whose latency
+// is lower).
+enum GemmPrec { GP_F64 = 0, GP_DF32 = 1, GP_TC64 = 2 };
+constexpr long long kTcMinMacs = 1ll << 24;
 
 template <class LA, class LB>
 inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha,
@@ -315,6 +331,9 @@ inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, d
                    const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr)
 {
     if (M <= 0 || N <= 0 || batch <= 0) return;
+    if (prec == GP_TC64 && (long long)M * N * K * batch >= kTcMinMacs &&
+        gemm_tc(st, M, N, K, A, B, alpha, beta, C, ldc, bsC, batch, dM, dN, dK))
+        return;
     auto tiles_of = [&](int T) {
         return (long long)((M + T - 1) / T) * ((N + T - 1) / T) * batch;
     };

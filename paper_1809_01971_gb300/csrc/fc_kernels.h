@@ -48,6 +48,8 @@ void launch_build_symbol(cudaStream_t st, int n, int d, const double* lam, const
 void launch_concat_normalize(cudaStream_t st, int d, int n, Piece p0, Piece p1, double* U,
                              int ldo, long long bsU, double* w);
 // Y[:, t] = |w_t| U[:, t] for t < K (batch over modes)
+// p[i + k*ld] *= w[k], i < rows, k < K (in place)
+void launch_scale_cols(cudaStream_t st, int rows, int K, double* p, int ld, const double* w);
 void launch_scale_cols_abs(cudaStream_t st, int d, int n, int K, const double* U, int ldu,
                            long long bsU, const double* w, double* Y, int ldy, long long bsY);
 // Y[:, (k,j)] = |xa_k xb_j| E[:,k] . Yh[:,j]  (explicit Khatri-Rao columns, K = Ra*S)

@@ -113,6 +113,25 @@ void launch_scale_cols_abs(cudaStream_t st, int d, int n, int K, const double* U
     note_launch(); scale_cols_abs_kernel<<<dim3(blocks, d), 256, 0, st>>>(n, K, U, ldu, bsU, w, Y, ldy, bsY);
 }
 
+// p[i + k*ld] *= w[k] for i < rows, k < K (in place)
+__global__ void scale_cols_kernel(int rows, int K, double* p, int ld, const double* w)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * K;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), k = (int)(e / rows);
+        p[i + (long long)k * ld] *= w[k];
+    }
+}
+
+void launch_scale_cols(cudaStream_t st, int rows, int K, double* p, int ld, const double* w)
+{
+    long long tot = (long long)rows * K;
+    if (tot <= 0) return;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    note_launch(); scale_cols_kernel<<<blocks, 256, 0, st>>>(rows, K, p, ld, w);
+}
+
 __global__ void kr_cols_kernel(int n, int Ra, int S, const double* E, int lde, long long bsE,
                                const double* xa, const double* Yh, int ldy, long long bsY,
                                const double* xb, int absw, double* Y, int ldo, long long bsO)

@@ -33,6 +33,7 @@ FC_ENAN = -5
 FC_ECUDA = -6
 FC_EWORKSPACE = -7
 FC_ESETUP = -8
+FC_ETIMEOUT = -9
 
 
 class fc_cp(C.Structure):
@@ -109,6 +110,7 @@ def lib() -> C.CDLL:
             "fc_prof_enable": (I, [I]),
             "fc_symeig": (I, [I, I, I, V, I, C.c_longlong, V, C.c_longlong, V, I, C.c_longlong, V]),
             "fc_prof_read": (I, [C.POINTER(C.c_longlong), C.POINTER(D), C.POINTER(D)]),
+            "fc_dgemm": (I, [I, I, I, I, I, I, D, V, I, V, I, D, V, I, V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -219,7 +221,8 @@ class Handle:
 def fc_setup(n, d, alpha, beta, gamma, eps, delta_sym=0.0, precond_rank=0, max_rank=0,
              max_tucker=0, max_input_rank=0, directional=False, precision=0,
              device="cuda") -> Handle:
-    """precision: 0 FP64 contractions, 1 double-float FP32 contractions (fc_setup_opts)."""
+    """precision: 0 FP64 contractions, 1 double-float FP32 contractions, 2 FP64-accurate
+    digit products on the BF16 tensor cores for the large contractions (fc_setup_opts)."""
     o = fc_setup_opts(delta_sym, precond_rank, max_rank, max_tucker, max_input_rank,
                       1 if directional else 0, int(precision))
     out = C.c_void_p()
@@ -358,6 +361,31 @@ def fc_symeig(A: torch.Tensor, method: int = 0, stream=None):
                                         C.c_void_p(w.data_ptr()), m, C.c_void_p(Vt.data_ptr()), m,
                                         m * m, _stream(stream)))
     return w, Vt.transpose(1, 2)
+
+
+def fc_dgemm(A: torch.Tensor, B: torch.Tensor, precision: int = 2, alpha: float = 1.0,
+             beta: float = 0.0, C_: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """C = alpha A B + beta C for FP64 CUDA matrices in a contraction form of the solver
+    (0 FP64, 1 double-float FP32, 2 BF16 tensor-core digit products).  A torch matrix in
+    row-major storage is the column-major transpose, so op(A) = A is passed as transA with
+    the row-major leading dimension."""
+    assert A.dtype == torch.float64 and B.dtype == torch.float64 and A.dim() == 2 and B.dim() == 2
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    if C_ is None:
+        C_ = torch.zeros(M, N, dtype=torch.float64, device=A.device)
+    assert C_.shape == (M, N) and C_.is_contiguous() and C_.dtype == torch.float64
+    # row-major C (M x N) is the column-major C^T (N x M, ld N) = B^T A^T, where the row-major
+    # B (K x N) is the column-major B^T (N x K, ld N) and A the column-major A^T (K x M, ld K)
+    _check("fc_dgemm", lib().fc_dgemm(int(precision), 0, 0, N, M, K, float(alpha),
+                                      C.c_void_p(B.data_ptr()), max(N, 1),
+                                      C.c_void_p(A.data_ptr()), max(K, 1), float(beta),
+                                      C.c_void_p(C_.data_ptr()), max(N, 1), _stream(stream)))
+    out = C_
+    return out
 
 
 PROF_JACOBI = 1

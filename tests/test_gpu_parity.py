@@ -196,9 +196,10 @@ def test_truncate_sketch_path_matches_oracle(fc, n, d, R, eps, rate):
     assert rel(Yf, Rf) <= 3.0 * eps + floor + 1e-13
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("n,d,S,which,eps", [(31, 2, 3, 0, 1e-8), (40, 3, 4, 0, 1e-7),
-                                             (40, 3, 4, 1, 1e-7), (64, 3, 8, 0, 1e-6)])
+                                             (40, 3, 4, 1, 1e-7), (64, 3, 8, 0, 1e-6),
+                                             (127, 3, 8, 0, 1e-8)])
 def test_apply_trunc_matches_oracle(fc, n, d, S, which, eps, precision):
     """trunc(fun(x)) / trunc(precond(x)) of Algorithm 1 with the Khatri-Rao columns kept
     implicit, against the oracle's truncation of the explicit mat-vec (normalize=False).
@@ -287,11 +288,12 @@ def test_solve_config1_2d(fc):
     assert e < 1e-7
 
 
-@pytest.mark.parametrize("problem,precision", [(0, 0), (3, 0), (4, 0), (5, 0), (1, 1), (5, 1)])
+@pytest.mark.parametrize("problem,precision", [(0, 0), (3, 0), (4, 0), (5, 0), (1, 1), (5, 1),
+                                                (2, 2), (5, 2)])
 def test_solve_config2_3d_n255(fc, problem, precision):
     """3D, n=255, 4 Gaussians + sine mode: CP-PCG vs the full oracle (16.6M points), at the
-    workload's settings (eps = 1e-9, tol = 1e-8, cap 192): error <= 1e-6, with FP64 and with
-    double-float contractions."""
+    workload's settings (eps = 1e-9, tol = 1e-8, cap 192): error <= 1e-6, with FP64,
+    double-float and tensor-core digit-product contractions."""
     prob = fi.config2(problem)
     info, e = _solve_vs_full(fc, prob, prob.tol, prob.eps, max_rank=prob.max_rank,
                              precision=precision)
