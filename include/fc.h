@@ -235,7 +235,8 @@ unsigned long long fc_launch_count(void);
  *  method 0: Householder tridiagonalisation, bisection, inverse iteration, back-transformation
  *            (FP64, eigenvalues accurate to ~u ||A|| in absolute terms);
  *  method 1: the truncation's solver for graded positive semi-definite Grams: Jacobi sweeps in
- *            FP32, eigenvectors made orthonormal in FP64 (to ~u) by Cholesky-QR in order of
+ *            FP32, eigenvectors made orthonormal (to ~1e-14: Gram and product in double-float,
+ *            Cholesky factor and its inverse in FP64) by Cholesky-QR in order of
  *            increasing eigenvalue; eigen-directions accurate relative to the grading, the
  *            eigenvalues FP64 Rayleigh quotients of the returned vectors. */
 int fc_symeig(int method, int batch, int m, const double* dev_A, int lda, long long strideA,

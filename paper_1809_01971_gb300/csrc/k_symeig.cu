@@ -348,22 +348,26 @@ symeig_kernel(const double* __restrict__ A, int lda, long long bsA, const int* _
 // ever absorbs components of smaller ones (never a large one leaking into a small one).
 // Eigenvalues: FP64 Rayleigh quotients of the final vectors if `rq`, else the FP32 values.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kEigThreads)
+constexpr int kGjThreads = 1024;
+
+__global__ void __launch_bounds__(kGjThreads, 1)
 gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* __restrict__ dims,
                int dstride, int cmax, double* __restrict__ ev, long long bsE,
                double* __restrict__ V, int ldv, long long bsV, int rq, float floorRel, int prof)
 {
     extern __shared__ double sm[];
     const int b = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
     int c = cmax;
     if (dims) c = min(dims[b * dstride], cmax);
     if (c < 0) c = 0;
     if (prof && tid == 0) atomicAdd(&g_prof_work, 9ull * (unsigned long long)c * c * c);
     const int S = kMaxC + 1;
-    double* A64 = sm;                      // c x S
-    double* V64 = A64 + kMaxC * S;         // c x S
-    double* G = V64 + kMaxC * S;           // c x S (Gram / Cholesky factor)
-    float* a = (float*)(G + kMaxC * S);    // m x S (FP32 working matrix)
+    double* A64 = sm;                      // c x S  input (FP64), for the Rayleigh quotients
+    double* G = A64 + kMaxC * S;           // c x S  Gram -> Cholesky factor L -> output vectors
+    double* Li = G + kMaxC * S;            // c x S  L^-1 (lower triangle)
+    float2* Lf = (float2*)(Li + kMaxC * S);   // c x S  L^-1 as double-float pairs
+    float* a = (float*)(Lf + kMaxC * S);   // m x S (FP32 working matrix)
     float* v = a + kMaxC * S;              // m x S (FP32 eigenvectors, row-major v[r*S+col])
     float* coefS = v + kMaxC * S;
     float* coefP = coefS + kMaxC;
@@ -389,10 +393,10 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         if (i == j) dmax = fmax(dmax, fabs(x));
     }
     dmax = warp_max(dmax);
-    if ((tid & 31) == 0) red[tid >> 5] = dmax;
+    if (lane == 0) red[wid] = dmax;
     __syncthreads();
     if (tid < 32) {
-        double t = (tid < (int)(blockDim.x >> 5)) ? red[tid] : 0.0;
+        double t = (tid < nwarp) ? red[tid] : 0.0;
         t = warp_max(t);
         if (tid == 0) red[0] = t;
     }
@@ -409,11 +413,12 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         a[i * S + j] = (i < c && j < c) ? (float)(A64[i * S + j] * sc) : 0.0f;
         v[i * S + j] = (i == j) ? 1.0f : 0.0f;
     }
-    __syncthreads();
 
     // ---- FP32 cyclic Jacobi, round-robin pairing (m/2 disjoint rotations per round) -------
     // pair i of round rnd: (rnd, m-1) for i = 0, else ((rnd+i) mod (m-1), (rnd-i) mod (m-1));
-    // the table is built once; each pair's rotation J = [[c, s], [-s, c]] acts on (p < q)
+    // the table is built once; each pair's rotation J = [[c, s], [-s, c]] acts on (p < q).
+    // One round: the m/2 rotation parameters (one warp), then every 2x2 block of A (J^T A J)
+    // and every row pair of V (V J) in one pass over the block's threads.
     const int half = m / 2;
     for (int e_ = tid; e_ < (m - 1) * half; e_ += blockDim.x) {
         const int rnd = e_ / half, i = e_ - rnd * half;
@@ -424,6 +429,7 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         pairs[e_] = p | (q << 8);
     }
     __syncthreads();
+    const int nblk = half * half, nwork = nblk + m * half;
     for (int sweep = 0; sweep < 15; ++sweep) {
         if (tid == 0) anyRot = 0;
         __syncthreads();
@@ -440,11 +446,11 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                 // entries carry no information; at most 15 sweeps (quadratic convergence:
                 // ~5 suffice for an ordering basis)
                 if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), floorRel)) {
-                    const float th = (aqq - app) / (2.0f * apq);
+                    const float th = __fdividef(aqq - app, 2.0f * apq);
                     float t;
-                    if (fabsf(th) > 1e18f) t = 0.5f / th;
-                    else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
-                    cs = rsqrtf(t * t + 1.0f);
+                    if (fabsf(th) > 1e18f) t = __fdividef(0.5f, th);
+                    else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+                    cs = rsqrtf(fmaf(t, t, 1.0f));
                     sn = t * cs;
                     rot = 1;
                 }
@@ -454,32 +460,34 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                 if (rot) anyRot = 1;
             }
             __syncthreads();
-            // A <- J^T A J, one 2x2 block (pair pi rows, pair pj columns) per thread-step
-            for (int e_ = tid; e_ < half * half; e_ += blockDim.x) {
-                const int pi = e_ % half, pj = e_ / half;
-                const int ri = rotated[pi], rj = rotated[pj];
-                if (!ri && !rj) continue;
-                const int p1 = pr[pi] & 255, q1 = pr[pi] >> 8, p2 = pr[pj] & 255, q2 = pr[pj] >> 8;
-                const float ci = coefS[pi], si = coefP[pi], cj = coefS[pj], sj = coefP[pj];
-                const float b00 = a[p1 * S + p2], b01 = a[p1 * S + q2];
-                const float b10 = a[q1 * S + p2], b11 = a[q1 * S + q2];
-                const float r00 = ci * b00 - si * b10, r01 = ci * b01 - si * b11;   // J_i^T B
-                const float r10 = si * b00 + ci * b10, r11 = si * b01 + ci * b11;
-                float o00 = cj * r00 - sj * r01, o01 = sj * r00 + cj * r01;        // (.) J_j
-                float o10 = cj * r10 - sj * r11, o11 = sj * r10 + cj * r11;
-                if (pi == pj) { o01 = 0.0f; o10 = 0.0f; }                     // annihilated
-                a[p1 * S + p2] = o00; a[p1 * S + q2] = o01;
-                a[q1 * S + p2] = o10; a[q1 * S + q2] = o11;
-            }
-            // V <- V J
-            for (int e_ = tid; e_ < m * half; e_ += blockDim.x) {
-                const int r = e_ % m, pi = e_ / m;
-                if (!rotated[pi]) continue;
-                const int p = pr[pi] & 255, q = pr[pi] >> 8;
-                const float c_ = coefS[pi], s_ = coefP[pi];
-                const float vp = v[r * S + p], vq = v[r * S + q];
-                v[r * S + p] = c_ * vp - s_ * vq;
-                v[r * S + q] = s_ * vp + c_ * vq;
+            for (int e_ = tid; e_ < nwork; e_ += blockDim.x) {
+                if (e_ < nblk) {
+                    // A <- J^T A J on the 2x2 block (pair pi rows, pair pj columns)
+                    const int pi = e_ % half, pj = e_ / half;
+                    const int ri = rotated[pi], rj = rotated[pj];
+                    if (!ri && !rj) continue;
+                    const int p1 = pr[pi] & 255, q1 = pr[pi] >> 8, p2 = pr[pj] & 255, q2 = pr[pj] >> 8;
+                    const float ci = coefS[pi], si = coefP[pi], cj = coefS[pj], sj = coefP[pj];
+                    const float b00 = a[p1 * S + p2], b01 = a[p1 * S + q2];
+                    const float b10 = a[q1 * S + p2], b11 = a[q1 * S + q2];
+                    const float r00 = ci * b00 - si * b10, r01 = ci * b01 - si * b11;   // J_i^T B
+                    const float r10 = si * b00 + ci * b10, r11 = si * b01 + ci * b11;
+                    float o00 = cj * r00 - sj * r01, o01 = sj * r00 + cj * r01;        // (.) J_j
+                    float o10 = cj * r10 - sj * r11, o11 = sj * r10 + cj * r11;
+                    if (pi == pj) { o01 = 0.0f; o10 = 0.0f; }                     // annihilated
+                    a[p1 * S + p2] = o00; a[p1 * S + q2] = o01;
+                    a[q1 * S + p2] = o10; a[q1 * S + q2] = o11;
+                } else {
+                    // V <- V J on row r, pair pi
+                    const int e2 = e_ - nblk;
+                    const int r = e2 % m, pi = e2 / m;
+                    if (!rotated[pi]) continue;
+                    const int p = pr[pi] & 255, q = pr[pi] >> 8;
+                    const float c_ = coefS[pi], s_ = coefP[pi];
+                    const float vp = v[r * S + p], vq = v[r * S + q];
+                    v[r * S + p] = c_ * vp - s_ * vq;
+                    v[r * S + q] = s_ * vp + c_ * vq;
+                }
             }
             __syncthreads();
         }
@@ -498,19 +506,19 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         order[rk] = i;
     }
     __syncthreads();
-    for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
-        const int r = e_ % c, j = e_ / c;                // V64[:, j] = v[:, order[j]]
-        V64[r * S + j] = (double)v[r * S + order[j]];
-    }
-    __syncthreads();
-
-    // ---- FP64 Cholesky-QR of V64 (columns in ascending order): V64 <- V64 L^-T ------------
+    // ---- orthonormalisation of W = v[:, order] (columns in ascending order) -------------
+    // Cholesky-QR W <- W L^-T with W^T W = L L^T.  W's entries are FP32 numbers, so the Gram
+    // is formed from exact products in double-float arithmetic (FP32 pipe) and rounded to
+    // FP64; Cholesky and L^-1 run in FP64; the product W L^-T again in double-float with
+    // L^-1 split into FP32 pairs.  Orthonormal to ~1e-14 (double-float rounding).
     for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
         const int i = e_ % c, j = e_ / c;
         if (i < j) continue;
-        double s_ = 0.0;
-        for (int r = 0; r < c; ++r) s_ = fma(V64[r * S + i], V64[r * S + j], s_);
-        G[i * S + j] = s_;                               // lower triangle of V^T V
+        const int oi = order[i], oj = order[j];
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int r = 0; r < c; ++r)
+            df_fma(acc, make_float2(v[r * S + oi], 0.0f), make_float2(v[r * S + oj], 0.0f));
+        G[i * S + j] = (double)acc.x + (double)acc.y;    // lower triangle of W^T W
     }
     __syncthreads();
     for (int k = 0; k < c; ++k) {
@@ -525,12 +533,32 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         }
         __syncthreads();
     }
-    for (int r = tid; r < c; r += blockDim.x) {            // row r: solve L y = V64[r, :]^T
-        for (int j = 0; j < c; ++j) {
-            double s_ = V64[r * S + j];
-            for (int i = 0; i < j; ++i) s_ = fma(-G[j * S + i], V64[r * S + i], s_);
-            V64[r * S + j] = s_ / G[j * S + j];
+    // L^-1 column by column, one warp per column j: x_j = 1 / L_jj,
+    // x_i = -(sum_{j <= k < i} L_ik x_k) / L_ii (lane-parallel dot products)
+    for (int j = wid; j < c; j += nwarp) {
+        if (lane == 0) Li[j * S + j] = 1.0 / G[j * S + j];
+        __syncwarp();
+        for (int i = j + 1; i < c; ++i) {
+            double s_ = 0.0;
+            for (int k = j + lane; k < i; k += 32) s_ = fma(G[i * S + k], Li[k * S + j], s_);
+            s_ = warp_sum(s_);
+            if (lane == 0) Li[i * S + j] = -s_ / G[i * S + i];
+            __syncwarp();
         }
+    }
+    __syncthreads();
+    for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
+        const int i = e_ % c, j = e_ / c;
+        if (j <= i) Lf[i * S + j] = df_split(Li[i * S + j]);
+    }
+    __syncthreads();
+    // G[r][j] = (W L^-T)[r, j] = sum_{k <= j} W[r, k] (L^-1)[j, k]
+    for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
+        const int r = e_ % c, j = e_ / c;
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int k = 0; k <= j; ++k)
+            df_fma(acc, make_float2(v[r * S + order[k]], 0.0f), Lf[j * S + k]);
+        G[r * S + j] = (double)acc.x + (double)acc.y;
     }
     __syncthreads();
 
@@ -541,8 +569,8 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
             lam = 0.0;
             for (int i = 0; i < c; ++i) {
                 double t = 0.0;
-                for (int k2 = 0; k2 < c; ++k2) t = fma(A64[i * S + k2], V64[k2 * S + j], t);
-                lam = fma(V64[i * S + j], t, lam);
+                for (int k2 = 0; k2 < c; ++k2) t = fma(A64[i * S + k2], G[k2 * S + j], t);
+                lam = fma(G[i * S + j], t, lam);
             }
         } else {
             lam = dmax * (double)a[order[j] * S + order[j]];
@@ -551,13 +579,13 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
     }
     for (int e_ = tid; e_ < c * c; e_ += blockDim.x) {
         const int r = e_ % c, j = e_ / c;
-        Vb[r + (long long)(c - 1 - j) * ldv] = V64[r * S + j];
+        Vb[r + (long long)(c - 1 - j) * ldv] = G[r * S + j];
     }
 }
 
 size_t gjacobi_smem() {
     const int S = kMaxC + 1;
-    return sizeof(double) * 3 * (size_t)kMaxC * S + sizeof(float) * (2 * (size_t)kMaxC * S + 2 * kMaxC) +
+    return sizeof(double) * 4 * (size_t)kMaxC * S + sizeof(float) * (2 * (size_t)kMaxC * S + 2 * kMaxC) +
            sizeof(int) * (2 * kMaxC + (size_t)kMaxC * kMaxC / 2);
 }
 
@@ -569,7 +597,7 @@ void launch_gjacobi(cudaStream_t st, int batch, const double* A, int lda, long l
     const bool prof = prof_active(KC_JACOBI);
     ProfMark mark;
     if (prof) prof_begin(st, mark);
-    note_launch(); gjacobi_kernel<<<batch, kEigThreads, gjacobi_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, rq ? 1 : 0, floorRel, prof ? 1 : 0);
+    note_launch(); gjacobi_kernel<<<batch, kGjThreads, gjacobi_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, rq ? 1 : 0, floorRel, prof ? 1 : 0);
     if (prof) prof_end(st, mark);
 }
 
