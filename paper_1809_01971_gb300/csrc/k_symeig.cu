@@ -369,10 +369,8 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
     float2* Lf = (float2*)(Li + kMaxC * S);   // c x S  L^-1 as double-float pairs
     float* a = (float*)(Lf + kMaxC * S);   // m x S (FP32 working matrix)
     float* v = a + kMaxC * S;              // m x S (FP32 eigenvectors, row-major v[r*S+col])
-    float* coefS = v + kMaxC * S;
-    float* coefP = coefS + kMaxC;
-    int* rotated = (int*)(coefP + kMaxC);
-    int* order = rotated + kMaxC;          // ascending eigenvalue order
+    float2* cso = (float2*)(v + kMaxC * S);  // (cos, sin) of each pair's rotation; sin = 0: none
+    int* order = (int*)(cso + kMaxC);      // ascending eigenvalue order
     int* pairs = order + kMaxC;            // (m-1) x m/2 round-robin pairs, p | q << 8
     __shared__ double red[32];
     __shared__ int anyRot;
@@ -429,22 +427,32 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         pairs[e_] = p | (q << 8);
     }
     __syncthreads();
+    // this thread's work items of a round, the same in every round (no index division in the
+    // sweeps): kind 0 = 2x2 block (pair pi rows, pair pj columns) of A, kind 1 = row r of V
+    // on pair pi; at most 3 items per thread (m <= 64: 32^2 + 64 * 32 <= 3 * 1024)
     const int nblk = half * half, nwork = nblk + m * half;
+    int itA[3], itB[3], nit = 0;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int e_ = tid + t * kGjThreads;
+        itA[t] = 0; itB[t] = 0;
+        if (e_ < nblk) { itA[t] = e_ % half; itB[t] = e_ / half; nit = t + 1; }
+        else if (e_ < nwork) { const int e2 = e_ - nblk; itA[t] = -1 - e2 % m; itB[t] = e2 / m; nit = t + 1; }
+    }
     for (int sweep = 0; sweep < 15; ++sweep) {
         if (tid == 0) anyRot = 0;
         __syncthreads();
         for (int rnd = 0; rnd < m - 1; ++rnd) {
             const int* pr = pairs + rnd * half;
             if (tid < half) {
-                const int p = pr[tid] & 255, q = pr[tid] >> 8;
+                const int pq = pr[tid];
+                const int p = pq & 255, q = pq >> 8;
                 const float app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
                 float cs = 1.0f, sn = 0.0f;
-                int rot = 0;
                 // relative threshold a few FP32 ulps above rounding noise, with a floor at
                 // floorRel of the largest diagonal entry: the rounding level of the FP64 Gram
                 // (1e-15 for a Gram formed normwise, ~1e-20 for a row-graded one), below which
-                // entries carry no information; at most 15 sweeps (quadratic convergence:
-                // ~5 suffice for an ordering basis)
+                // entries carry no information; at most 15 sweeps
                 if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), floorRel)) {
                     const float th = __fdividef(aqq - app, 2.0f * apq);
                     float t;
@@ -452,22 +460,22 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                     else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
                     cs = rsqrtf(fmaf(t, t, 1.0f));
                     sn = t * cs;
-                    rot = 1;
+                    if (sn != 0.0f) anyRot = 1;
                 }
-                coefS[tid] = cs;
-                coefP[tid] = sn;
-                rotated[tid] = rot;
-                if (rot) anyRot = 1;
+                cso[tid] = make_float2(cs, sn);
             }
             __syncthreads();
-            for (int e_ = tid; e_ < nwork; e_ += blockDim.x) {
-                if (e_ < nblk) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t >= nit) break;
+                if (itA[t] >= 0) {
                     // A <- J^T A J on the 2x2 block (pair pi rows, pair pj columns)
-                    const int pi = e_ % half, pj = e_ / half;
-                    const int ri = rotated[pi], rj = rotated[pj];
-                    if (!ri && !rj) continue;
-                    const int p1 = pr[pi] & 255, q1 = pr[pi] >> 8, p2 = pr[pj] & 255, q2 = pr[pj] >> 8;
-                    const float ci = coefS[pi], si = coefP[pi], cj = coefS[pj], sj = coefP[pj];
+                    const int pi = itA[t], pj = itB[t];
+                    const float2 ki = cso[pi], kj = cso[pj];
+                    if (ki.y == 0.0f && kj.y == 0.0f) continue;
+                    const int pqi = pr[pi], pqj = pr[pj];
+                    const int p1 = pqi & 255, q1 = pqi >> 8, p2 = pqj & 255, q2 = pqj >> 8;
+                    const float ci = ki.x, si = ki.y, cj = kj.x, sj = kj.y;
                     const float b00 = a[p1 * S + p2], b01 = a[p1 * S + q2];
                     const float b10 = a[q1 * S + p2], b11 = a[q1 * S + q2];
                     const float r00 = ci * b00 - si * b10, r01 = ci * b01 - si * b11;   // J_i^T B
@@ -479,14 +487,13 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                     a[q1 * S + p2] = o10; a[q1 * S + q2] = o11;
                 } else {
                     // V <- V J on row r, pair pi
-                    const int e2 = e_ - nblk;
-                    const int r = e2 % m, pi = e2 / m;
-                    if (!rotated[pi]) continue;
-                    const int p = pr[pi] & 255, q = pr[pi] >> 8;
-                    const float c_ = coefS[pi], s_ = coefP[pi];
+                    const int r = -1 - itA[t], pi = itB[t];
+                    const float2 k_ = cso[pi];
+                    if (k_.y == 0.0f) continue;
+                    const int pq = pr[pi], p = pq & 255, q = pq >> 8;
                     const float vp = v[r * S + p], vq = v[r * S + q];
-                    v[r * S + p] = c_ * vp - s_ * vq;
-                    v[r * S + q] = s_ * vp + c_ * vq;
+                    v[r * S + p] = k_.x * vp - k_.y * vq;
+                    v[r * S + q] = k_.y * vp + k_.x * vq;
                 }
             }
             __syncthreads();
@@ -585,8 +592,8 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
 
 size_t gjacobi_smem() {
     const int S = kMaxC + 1;
-    return sizeof(double) * 4 * (size_t)kMaxC * S + sizeof(float) * (2 * (size_t)kMaxC * S + 2 * kMaxC) +
-           sizeof(int) * (2 * kMaxC + (size_t)kMaxC * kMaxC / 2);
+    return sizeof(double) * 4 * (size_t)kMaxC * S + sizeof(float) * 2 * (size_t)kMaxC * S +
+           sizeof(float2) * kMaxC + sizeof(int) * (kMaxC + (size_t)kMaxC * kMaxC / 2);
 }
 
 void launch_gjacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
