@@ -177,6 +177,12 @@ def run_reference(args):
 # FP64 peak of the chip from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
 # x 2 flop x 2.07 GHz (an FP64 probe on this part measured 1.19 TFLOP/s at 1.9-2.07 GHz).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# Dense BF16 tensor throughput of the GB300s, measured and sustained over seconds
+# (cuBLAS 8192^3, MEASURED_PEAKS.json): the tensor-pipe peak of a kernel timed in a long step.
+BF16_PEAK_SUSTAINED_TFLOPS = 1686.8
+# Tensor-core contraction DRAM traffic per launch from one ncu capture; None when not captured
+# for the current kernel.
+TC_TRAFFIC_BYTES = None
 # Eigen-solver DRAM traffic per launch (dram__bytes_read.sum + write) from one ncu capture of
 # the current kernel (3-matrix launch of the n=255 solve); None when not captured for it.
 EIG_TRAFFIC_BYTES = None
@@ -287,9 +293,17 @@ def main():
         for h, U, u in zip(hs, Us, full_u):
             fc.fc_to_full(h, U, out=tmp)
             err = max(err, float(torch.linalg.norm(tmp - u) / torch.linalg.norm(u)))
+        tc_prof = None
+        if form == 2:
+            # the tensor-core contraction class, instrumented over extra (untimed) steps
+            fc.fc_prof_enable(fc.fc.PROF_TC)
+            tc_times = [timed(step)[0] for _ in range(args.steps)]
+            tc_prof = fc.fc_prof_read() + (sum(tc_times),)
+            barrier()
         results[form] = {"hs": hs, "Us": Us, "step": step, "t_total": t_total,
                          "value": len(probs) * args.steps * world / t_total,
-                         "launches": launches, "prof": prof, "iters": iters[-1], "err": err}
+                         "launches": launches, "prof": prof, "iters": iters[-1], "err": err,
+                         "tc_prof": tc_prof}
     clocks = sampler.stop()
 
     ok = [f for f in results if results[f]["err"] <= args.max_err]
@@ -356,6 +370,19 @@ def main():
                     "launches": jac_n, "avg_launch_us": 1e3 * jac_ms / jac_n,
                     "event_ms_over_step_ms": jac_ms / (t_total * 1e3),
                     "note": "launches overlap across the problem streams, so summed event time can exceed step time"}
+    roofline_tc = None
+    if results[2]["tc_prof"] and results[2]["tc_prof"][0] > 0:
+        tn, tms, twork, tstep_ms = results[2]["tc_prof"]
+        achieved = twork / tn / (tms / tn * 1e-3) / 1e12
+        peak = BF16_PEAK_SUSTAINED_TFLOPS
+        roofline_tc = {"kernel": "gemm_tc_kernel (FP64 contractions of the tc64 form as BF16 "
+                                 "digit-pair MMAs on tcgen05, TMEM accumulators)",
+                       "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": TC_TRAFFIC_BYTES,
+                       "peak_kind": "measured BF16 dense, sustained (MEASURED_PEAKS.json)",
+                       "work": "BF16 MMA flops issued: 36 digit pairs x 2 x 128 x N_tile per K",
+                       "launches": tn, "avg_launch_us": 1e3 * tms / tn,
+                       "event_ms_over_step_ms": tms / tstep_ms}
     if rank == 0:
         name, dtype, what = FORMS[best]
         forms = {FORMS[f][0]: {"value": results[f]["value"], "unit": UNIT,
@@ -383,6 +410,7 @@ def main():
                 "gpu_launches": int(R["launches"]),
                 "clocks": clocks,
                 "roofline": roofline,
+                "roofline_tc": roofline_tc,
                 "cpu_baseline": None}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(probs)

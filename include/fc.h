@@ -258,7 +258,9 @@ int fc_dgemm(int precision, int transA, int transB, int M, int N, int K, double 
 /* Kernel-class instrumentation.  fc_prof_enable(kclass) synchronises the device, clears the
  * counters and, until fc_prof_read, brackets every launch of that class with a pair of CUDA
  * events on its stream and accumulates the class's algorithmic work on the device.
- * kclass: 0 = off, 1 = the FP64 small eigen-solver (work = 9 c^3 flops per c x c matrix).
+ * kclass: 0 = off, 1 = the small eigen-solver (work = 9 c^3 flops per c x c matrix),
+ * 2 = the tensor-core contraction (work = BF16 MMA flops issued: 36 digit-pair products per
+ * multiply-add of the FP64 contraction, tiles padded to 128 x N).
  * fc_prof_read disables it, synchronises, and returns the launches, the summed event time of
  * those launches in ms, and the work (flops). */
 int fc_prof_enable(int kclass);

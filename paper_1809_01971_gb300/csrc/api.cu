@@ -676,7 +676,7 @@ int fc_dgemm(int precision, int transA, int transB, int M, int N, int K, double 
 }
 
 int fc_prof_enable(int kclass) {
-    if (kclass < 0 || kclass > KC_JACOBI) return FC_EINVAL;
+    if (kclass < 0 || kclass > KC_TC) return FC_EINVAL;
     std::lock_guard<std::mutex> lock(g_prof_mu);
     if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError());
     g_prof_used = 0;

@@ -14,7 +14,7 @@ void note_launch();
 
 // Kernel-class timing for instrumentation (fc_prof_*): while a class is enabled, each of
 // its launches is bracketed by a pair of CUDA events recorded on the launching stream.
-enum KernelClass { KC_NONE = 0, KC_JACOBI = 1 };
+enum KernelClass { KC_NONE = 0, KC_JACOBI = 1, KC_TC = 2 };
 struct ProfMark { int slot = -1; };
 bool prof_active(int kclass);
 void prof_begin(cudaStream_t st, ProfMark& m);

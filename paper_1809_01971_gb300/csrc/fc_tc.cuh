@@ -331,7 +331,7 @@ template <int BN, class LA, class LB>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
                LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
-               int batch, int splits, int kchunk)
+               int batch, int splits, int kchunk, unsigned long long* work)
 {
     using Sh = TcShape<BN>;
     constexpr int S = kTcDigits;
@@ -512,6 +512,10 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
                 else *c = (beta == 0.0) ? v : v + beta * (*c);
             }
         }
+        // instrumentation: BF16 MMA flops issued by this CTA (36 digit pairs per K step)
+        if (work && tid == 0)
+            atomicAdd(work, (unsigned long long)(S * (S + 1) / 2) * 2ull * kTcBM * BN *
+                                (unsigned long long)(nst * kTcKS));
     } else if (tid == 0) {
         atomicExch(&g_tc_error, 1);
     }
@@ -573,25 +577,30 @@ inline bool gemm_tc(cudaStream_t st, int M, int N, int K, LA A, LB B, double alp
         note_launch(); gemm_prescale_kernel<<<g, 256, 0, st>>>(M, N, dM, dN, beta, C, ldc, bsC);
     }
     dim3 grid((M + kTcBM - 1) / kTcBM, (N + BN - 1) / BN, batch * splits);
+    const bool prof = prof_active(KC_TC);
+    unsigned long long* work = prof ? prof_work_counter() : nullptr;
+    ProfMark mark;
+    if (prof) prof_begin(st, mark);
     note_launch();
     switch (BN) {
         case 16:
             gemm_tc_kernel<16, LA, LB><<<grid, kTcThreads, TcShape<16>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
         case 32:
             gemm_tc_kernel<32, LA, LB><<<grid, kTcThreads, TcShape<32>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
         case 48:
             gemm_tc_kernel<48, LA, LB><<<grid, kTcThreads, TcShape<48>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
         default:
             gemm_tc_kernel<64, LA, LB><<<grid, kTcThreads, TcShape<64>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
     }
+    if (prof) prof_end(st, mark);
     return true;
 }
 
