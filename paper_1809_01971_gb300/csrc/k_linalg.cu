@@ -70,13 +70,22 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
             }
             __syncwarp();
         }
-        const double lkk = sqrt(best);
-        const double ik = 1.0 / lkk;
+        const double ik = fc_rsqrt(best);
+        const double lkk = best * ik;
         if (lane == 0) { L[k * SS + k] = lkk; invd[k] = ik; }
         const int pk = perm[k];
         for (int i = k + 1 + lane; i < c; i += 32) {
-            double s0 = Mi[perm[i] * SS + pk];
-            for (int j = 0; j < k; ++j) s0 = fma(-L[i * SS + j], L[k * SS + j], s0);
+            // four independent accumulators: a dependent FP64 FMA costs 64 cycles on GB300
+            double s0 = Mi[perm[i] * SS + pk], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int j = 0;
+            for (; j + 4 <= k; j += 4) {
+                s0 = fma(-L[i * SS + j], L[k * SS + j], s0);
+                s1 = fma(-L[i * SS + j + 1], L[k * SS + j + 1], s1);
+                s2 = fma(-L[i * SS + j + 2], L[k * SS + j + 2], s2);
+                s3 = fma(-L[i * SS + j + 3], L[k * SS + j + 3], s3);
+            }
+            for (; j < k; ++j) s0 = fma(-L[i * SS + j], L[k * SS + j], s0);
+            s0 = (s0 + s1) + (s2 + s3);
             const double l = s0 * ik;
             L[i * SS + k] = l;
             dg[perm[i]] -= l * l;
@@ -89,8 +98,16 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
         for (int i = 0; i < j; ++i) Li[i * SS + j] = 0.0;
         Li[j * SS + j] = invd[j];
         for (int i = j + 1; i < r; ++i) {
-            double s0 = 0.0;
-            for (int t = j; t < i; ++t) s0 = fma(-L[i * SS + t], Li[t * SS + j], s0);
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int t = j;
+            for (; t + 4 <= i; t += 4) {
+                s0 = fma(-L[i * SS + t], Li[t * SS + j], s0);
+                s1 = fma(-L[i * SS + t + 1], Li[(t + 1) * SS + j], s1);
+                s2 = fma(-L[i * SS + t + 2], Li[(t + 2) * SS + j], s2);
+                s3 = fma(-L[i * SS + t + 3], Li[(t + 3) * SS + j], s3);
+            }
+            for (; t < i; ++t) s0 = fma(-L[i * SS + t], Li[t * SS + j], s0);
+            s0 = (s0 + s1) + (s2 + s3);
             Li[i * SS + j] = s0 * invd[i];
         }
     }

@@ -373,7 +373,9 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
     int* order = (int*)(cso + kMaxC);      // ascending eigenvalue order
     int* pairs = order + kMaxC;            // (m-1) x m/2 round-robin pairs, p | q << 8
     __shared__ double red[32];
+    __shared__ double dinv[kMaxC];         // 1 / L_kk of the Cholesky-QR
     __shared__ int anyRot;
+    __shared__ int roundRot[kMaxC];        // per round of a sweep: some pair rotates
 
     const double* Ab = A + b * bsA;
     double* evb = ev + b * bsE;
@@ -444,7 +446,9 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         __syncthreads();
         for (int rnd = 0; rnd < m - 1; ++rnd) {
             const int* pr = pairs + rnd * half;
-            if (tid < half) {
+            if (tid < 32) {
+              bool rot_ = false;
+              if (tid < half) {
                 const int pq = pr[tid];
                 const int p = pq & 255, q = pq >> 8;
                 const float app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
@@ -463,8 +467,15 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
                     if (sn != 0.0f) anyRot = 1;
                 }
                 cso[tid] = make_float2(cs, sn);
+                rot_ = (sn != 0.0f);
+              }
+              const unsigned any_ = __ballot_sync(0xffffffffu, rot_);
+              if (tid == 0) roundRot[rnd] = (any_ != 0u);
             }
             __syncthreads();
+            // a round without rotations writes nothing: no apply pass, no second barrier
+            // (the next round's rotation pass only reads what this round left unchanged)
+            if (!roundRot[rnd]) continue;
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 if (t >= nit) break;
@@ -529,10 +540,14 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
     }
     __syncthreads();
     for (int k = 0; k < c; ++k) {
-        if (tid == 0) G[k * S + k] = sqrt(fmax(G[k * S + k], 1e-300));
+        if (tid == 0) {
+            const double g = fmax(G[k * S + k], 1e-300), y = fc_rsqrt(g);
+            G[k * S + k] = g * y;
+            dinv[k] = y;
+        }
         __syncthreads();
-        const double lkk = G[k * S + k];
-        for (int i = k + 1 + tid; i < c; i += blockDim.x) G[i * S + k] /= lkk;
+        const double ik = dinv[k];
+        for (int i = k + 1 + tid; i < c; i += blockDim.x) G[i * S + k] *= ik;
         __syncthreads();
         for (int e_ = tid; e_ < (c - k - 1) * (c - k - 1); e_ += blockDim.x) {
             const int i = k + 1 + e_ % (c - k - 1), j = k + 1 + e_ / (c - k - 1);
@@ -543,13 +558,13 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
     // L^-1 column by column, one warp per column j: x_j = 1 / L_jj,
     // x_i = -(sum_{j <= k < i} L_ik x_k) / L_ii (lane-parallel dot products)
     for (int j = wid; j < c; j += nwarp) {
-        if (lane == 0) Li[j * S + j] = 1.0 / G[j * S + j];
+        if (lane == 0) Li[j * S + j] = dinv[j];
         __syncwarp();
         for (int i = j + 1; i < c; ++i) {
             double s_ = 0.0;
             for (int k = j + lane; k < i; k += 32) s_ = fma(G[i * S + k], Li[k * S + j], s_);
             s_ = warp_sum(s_);
-            if (lane == 0) Li[i * S + j] = -s_ / G[i * S + i];
+            if (lane == 0) Li[i * S + j] = -s_ * dinv[i];
             __syncwarp();
         }
     }
