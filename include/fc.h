@@ -82,6 +82,13 @@ typedef struct fc_setup_opts {
                         /* (8 digits, FP32-exact accumulation, error below FP64 rounding of  */
                         /* the row/column scales).  Eigen-solves, sketch Grams and scalars   */
                         /* stay FP64 in every form [0]                                        */
+    int op_kind;        /* operator (Section 6, Tables 6.1-6.4): 0 the control operator      */
+                        /* beta^2 A^-alpha + gamma A^alpha (A^alpha + A^-alpha at beta =      */
+                        /* gamma = 1); 1 A^alpha; 2 I + A^(2 alpha) (needs 2 alpha <= 1).     */
+                        /* beta, gamma enter only kind 0; fc_state needs kind 0 [0]           */
+    int precond_kind;   /* 0: least-squares exponential sum of 1/g (rank precond_rank);       */
+                        /* 1: the sinc-quadrature sum of rho^-alpha (the symbol g_1 of        */
+                        /* Section 6, the exact inverse of A^alpha) [0]                        */
 } fc_setup_opts;
 
 typedef struct fc_setup_info {
@@ -119,7 +126,7 @@ typedef struct fc_solve_info {
 /* Build the spectrum (eqn:eig_lap), the CP symbol of beta^2 rho^-alpha + gamma rho^alpha by
  * sinc quadrature of the Laplace transform (Section 4.2, eqn:Sinc_quadr_trunc, eqn:Func_of_rho;
  * the positive power through Lemma 4.1), and the exponential-sum preconditioner of 1/g.
- * Requires 0 < alpha <= 1, beta > 0, gamma > 0, d in {2,3}, 1 <= n <= 4095, eps > 0.
+ * Requires 0 < alpha <= 1, beta > 0, gamma > 0, d in {2,3}, 1 <= n <= 8191, eps > 0.
  * Allocates the handle's device tables (cudaMalloc on the current device). */
 int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
              const fc_setup_opts* opts, fc_handle* out);

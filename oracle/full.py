@@ -6,6 +6,8 @@ solve_full:  u = (F_1 x ... x F_d) diag(1/g(rho)) (F_1 x ... x F_d) b, the exact
 brute_force: dense A = sum_l I x A_(l) x I (eqn_low_rank_lap), symmetric
              eigendecomposition, A^{+-alpha} by the spectral definition
              (eqn:frac_Oper), dense solve.  Independent of the DST; n <= 16.
+g_operator / solve_full_op / brute_force_op: the same for the test operators of Section 6
+             (Tables 6.1-6.4): A^alpha and I + A^(2 alpha), besides the control operator.
 """
 from __future__ import annotations
 
@@ -97,3 +99,37 @@ def brute_force_power(ns, s) -> np.ndarray:
     A = dense_laplacian(ns)
     w, V = np.linalg.eigh(A)
     return V @ np.diag(w**s) @ V.T
+
+
+def g_operator(rho, kind, alpha, beta=1.0, gamma_=1.0):
+    """Symbol of the operator: kind 0 beta^2 rho^-alpha + gamma rho^alpha (the control
+    operator; A^alpha + A^-alpha at beta = gamma = 1), kind 1 rho^alpha (A^alpha), kind 2
+    1 + rho^(2 alpha) (I + A^(2 alpha))."""
+    if kind == 0:
+        return g_control(rho, alpha, beta, gamma_)
+    if kind == 1:
+        return rho ** alpha
+    if kind == 2:
+        return 1.0 + rho ** (2.0 * alpha)
+    raise ValueError(kind)
+
+
+def solve_full_op(b: np.ndarray, kind, alpha, beta=1.0, gamma_=1.0) -> np.ndarray:
+    """Exact solution of L u = b, L the operator of `kind`, in the DST-I eigenbasis."""
+    return apply_g_full(b, lambda r: 1.0 / g_operator(r, kind, alpha, beta, gamma_))
+
+
+def brute_force_op(b: np.ndarray, kind, alpha, beta=1.0, gamma_=1.0) -> np.ndarray:
+    """Dense solve with the operator assembled from the dense A by its eigendecomposition:
+    A^alpha, I + A^(2 alpha) or beta^2 A^-alpha + gamma A^alpha (no DST involved)."""
+    A = dense_laplacian(b.shape)
+    w, V = np.linalg.eigh(A)
+    if kind == 0:
+        f = beta**2 * w ** (-alpha) + gamma_ * w**alpha
+    elif kind == 1:
+        f = w**alpha
+    elif kind == 2:
+        f = 1.0 + w ** (2.0 * alpha)
+    else:
+        raise ValueError(kind)
+    return np.linalg.solve(V @ np.diag(f) @ V.T, b.reshape(-1)).reshape(b.shape)

@@ -116,6 +116,7 @@ struct fc_ctx {
     // state symbol beta rho^-alpha: the first RS columns of EA with weights xiA / beta
     double *xiS = nullptr, *GES = nullptr;
     int RS = 0;
+    SymbolSpec spec;      // operator symbol g(rho) = a rho^-sn + b rho^sp + c
     double alpha_eff = 0.0;   // exponent of the symbol's spectrum (1 for the directional operator)
     int prec = GP_F64;        // contractions in FP64 or double-float FP32 (fc_setup_opts.precision)
     // compressed mode factors of the three symbols (operator, preconditioner, state):
@@ -231,6 +232,7 @@ int compress_symbols(fc_ctx* h) {
     std::vector<Compressed> comp(3 * d);
     for (int sy = 0; sy < 3; ++sy) {
         const int R = Rs[sy];
+        if (R == 0) continue;                 // no state symbol for the test operators
         std::vector<double> E((size_t)n * R), xa(R);
         CK(cudaMemcpy(xa.data(), xdev[sy], sizeof(double) * R, cudaMemcpyDeviceToHost));
         for (int l = 0; l < d; ++l) {
@@ -715,12 +717,16 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
              const fc_setup_opts* o, fc_handle* out) {
     if (!out) return FC_EINVAL;
     *out = nullptr;
-    if (!(d == 2 || d == 3) || n < 1 || n > 4095 || !(alpha > 0.0 && alpha <= 1.0) ||
+    if (!(d == 2 || d == 3) || n < 1 || n > 8191 || !(alpha > 0.0 && alpha <= 1.0) ||
         !(beta > 0.0) || !(gamma > 0.0) || !(eps > 0.0) || !std::isfinite(beta) ||
         !std::isfinite(gamma))
         return FC_EINVAL;
-    fc_setup_opts opts{1e-10, 24, 32, 48, 0, 0, 0};
+    fc_setup_opts opts{1e-10, 24, 32, 48, 0, 0, 0, 0, 0};
     if (o) {
+        if (!(o->op_kind >= 0 && o->op_kind <= 2) || !(o->precond_kind == 0 || o->precond_kind == 1))
+            return FC_EINVAL;
+        opts.op_kind = o->op_kind;
+        opts.precond_kind = o->precond_kind;
         opts.directional = o->directional ? 1 : 0;
         opts.precision = (o->precision == 1 || o->precision == 2) ? o->precision : 0;
         if (o->delta_sym > 0) opts.delta_sym = o->delta_sym;
@@ -742,13 +748,28 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         for (double& x : lam) x = std::pow(x, alpha);
         alpha_eff = 1.0;
     }
+    // operator symbol: the control operator, or a test operator of Section 6
+    SymbolSpec gs;
+    if (opts.op_kind == 0) {
+        gs.a = beta * beta; gs.sn = alpha_eff; gs.b = gamma; gs.sp = alpha_eff;
+    } else if (opts.op_kind == 1) {                 // A^alpha
+        gs.b = 1.0; gs.sp = alpha_eff;
+    } else {                                        // I + A^(2 alpha), 2 alpha <= 1
+        if (2.0 * alpha_eff > 1.0) return FC_EINVAL;
+        gs.b = 1.0; gs.sp = 2.0 * alpha_eff; gs.c = 1.0;
+    }
     SymbolNodes sym, pc;
-    if (!build_control_nodes(lam, d, alpha_eff, beta, gamma, opts.delta_sym, sym)) return FC_ESETUP;
-    if (!build_precond_nodes(lam, d, alpha_eff, beta, gamma, opts.precond_rank, pc)) return FC_ESETUP;
+    if (!build_symbol_nodes(lam, d, gs, opts.delta_sym, sym)) return FC_ESETUP;
+    if (opts.precond_kind == 1) {
+        if (!build_inverse_power_nodes(lam, d, alpha_eff, opts.delta_sym, pc)) return FC_ESETUP;
+    } else if (!build_precond_nodes(lam, d, gs, opts.precond_rank, pc)) {
+        return FC_ESETUP;
+    }
     fc_ctx* h = new (std::nothrow) fc_ctx();
     if (!h) return FC_EINVAL;
     h->n = n; h->d = d; h->alpha = alpha; h->beta = beta; h->gamma = gamma; h->eps = eps;
     h->alpha_eff = alpha_eff;
+    h->spec = gs;
     h->prec = (opts.precision == 2) ? GP_TC64 : (opts.precision == 1) ? GP_DF32 : GP_F64;
     h->opts = opts;
     h->RA = (int)sym.tau.size();
@@ -943,12 +964,13 @@ int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int norma
 }
 
 int fc_state(fc_handle h, const fc_cp* u, double eps, int max_rank, fc_cp* y, void* stream) {
+    if (!h || h->RS == 0) return FC_EINVAL;   // only the control operator has a state symbol
     return fc_apply_trunc(h, 2, u, eps, max_rank, y, stream);
 }
 
 int fc_apply_trunc(fc_handle h, int which, const fc_cp* x, double eps, int max_rank, fc_cp* y,
                    void* stream) {
-    if (!h || !(which >= 0 && which <= 2) || !check_cp(h, x, false) || !check_cp(h, y, true) ||
+    if (!h || !(which >= 0 && which <= 2) || (which == 2 && h->RS == 0) || !check_cp(h, x, false) || !check_cp(h, y, true) ||
         !(eps >= 0.0) || max_rank < 1)
         return FC_EINVAL;
     if (!h->ws) return FC_EWORKSPACE;
@@ -1125,7 +1147,8 @@ int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev
     };
     int rc = dst_all(dev_rhs, dev_u);
     if (rc) return rc;
-    launch_full_scale(st, h->d, n, h->lam, h->alpha_eff, h->beta, h->gamma, dev_u);
+    launch_full_scale(st, h->d, n, h->lam, h->spec.a, h->spec.sn, h->spec.b, h->spec.sp,
+                      h->spec.c, dev_u);
     rc = dst_all(dev_u, dev_u);
     if (rc) return rc;
     CKL();

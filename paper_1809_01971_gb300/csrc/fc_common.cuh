@@ -42,7 +42,7 @@ struct LdT {  // op(X) = X^T
 struct LdSine {
     const double* tab; int N2;
     FC_DEV double operator()(int i, int k, int) const {
-        // (i+1)(k+1) <= (n+1)^2 < 2^31 for n <= 4095: 32-bit arithmetic
+        // (i+1)(k+1) <= (n+1)^2 <= 2^26 for n <= 8191: 32-bit arithmetic
         const unsigned m = (unsigned)(i + 1) * (unsigned)(k + 1);
         return tab[m % (unsigned)N2];
     }

@@ -97,9 +97,9 @@ void launch_inner_reduce(cudaStream_t st, int d, int Rx, int Ry, const double* x
                          const double* eta, const double* M, int ldm, long long bsM, double* out);
 void launch_to_full(cudaStream_t st, int d, int n, int R, const double* xi, const double* U0,
                     const double* U1, const double* U2, int ld, double* dense);
-// u_hat[i] /= g(rho_i) (full-format eigenbasis solve)
-void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double alpha,
-                       double beta, double gamma, double* x);
+// u_hat[i] /= g(rho_i), g = ga rho^-sn + gb rho^sp + gc (full-format eigenbasis solve)
+void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double ga, double sn,
+                       double gb, double sp, double gc, double* x);
 void launch_copy_weights(cudaStream_t st, int K, const double* src, double scale, double* dst);
 // w[(k,j)] = xa[k] * xb[j]
 void launch_outer_weights(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,

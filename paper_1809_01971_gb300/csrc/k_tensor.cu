@@ -475,8 +475,8 @@ void launch_to_full(cudaStream_t st, int d, int n, int R, const double* xi, cons
     note_launch(); to_full_kernel<<<blocks, 256, 0, st>>>(d, n, R, xi, U0, U1, U2, ld, dense);
 }
 
-__global__ void full_scale_kernel(int d, int n, const double* lam, double alpha, double beta,
-                                  double gamma, double* x)
+__global__ void full_scale_kernel(int d, int n, const double* lam, double ga, double sn,
+                                  double gb, double sp, double gc, double* x)
 {
     const long long tot = (d == 3) ? (long long)n * n * n : (long long)n * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
@@ -486,18 +486,20 @@ __global__ void full_scale_kernel(int d, int n, const double* lam, double alpha,
         int i1 = (int)(rest % n);
         int i2 = (int)(rest / n);
         double rho = lam[i0] + lam[i1] + (d == 3 ? lam[i2] : 0.0);
-        double g = beta * beta * pow(rho, -alpha) + gamma * pow(rho, alpha);
+        double g = gc;
+        if (ga != 0.0) g += ga * pow(rho, -sn);
+        if (gb != 0.0) g += gb * pow(rho, sp);
         x[e] /= g;
     }
 }
 
-void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double alpha,
-                       double beta, double gamma, double* x)
+void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double ga, double sn,
+                       double gb, double sp, double gc, double* x)
 {
     long long tot = (d == 3) ? (long long)n * n * n : (long long)n * n;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 152 * 64) blocks = 152 * 64;
-    note_launch(); full_scale_kernel<<<blocks, 256, 0, st>>>(d, n, lam, alpha, beta, gamma, x);
+    note_launch(); full_scale_kernel<<<blocks, 256, 0, st>>>(d, n, lam, ga, sn, gb, sp, gc, x);
 }
 
 __global__ void copy_weights_kernel(int K, const double* src, double scale, double* dst)

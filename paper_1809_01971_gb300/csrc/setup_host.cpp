@@ -142,67 +142,90 @@ ExpSum exp_sum(double s, double B, double delta, double s0) {
     return out;
 }
 
-double g_exact(double rho, double alpha, double beta, double gamma) {
-    return beta * beta * std::pow(rho, -alpha) + gamma * std::pow(rho, alpha);
+double SymbolSpec::eval(double rho) const {
+    double g = c;
+    if (a != 0.0) g += a * std::pow(rho, -sn);
+    if (b != 0.0) g += b * std::pow(rho, sp);
+    return g;
 }
 
-bool build_control_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
-                         double gamma, double delta, SymbolNodes& out) {
+bool build_symbol_nodes(const std::vector<double>& lam, int d, const SymbolSpec& g, double delta,
+                        SymbolNodes& out) {
     const int n = (int)lam.size();
     const double rmin = d * lam[0], rmax = d * lam[n - 1];
     const double B = rmax / rmin;
     out = SymbolNodes();
     out.rho_min = rmin;
     out.rho_max = rmax;
-    ExpSum em = exp_sum(alpha, B, delta, 0.5);
-    if (em.t.empty()) return false;
-    for (size_t k = 0; k < em.t.size(); ++k) {
-        out.tau.push_back(em.t[k] / rmin);
-        out.w.push_back(beta * beta * em.c[k] * std::pow(rmin, -alpha));
-        out.mode.push_back(-1);
+    ExpSum em, ep;
+    if (g.a != 0.0) {
+        em = exp_sum(g.sn, B, delta, 0.5);
+        if (em.t.empty()) return false;
+        for (size_t k = 0; k < em.t.size(); ++k) {
+            out.tau.push_back(em.t[k] / rmin);
+            out.w.push_back(g.a * em.c[k] * std::pow(rmin, -g.sn));
+            out.mode.push_back(-1);
+        }
     }
-    out.r_minus = (int)em.t.size();
-    if (alpha < 1.0) {
-        ExpSum ep = exp_sum(1.0 - alpha, B, delta, 0.5);
-        if (ep.t.empty()) return false;
-        for (size_t k = 0; k < ep.t.size(); ++k)
-            for (int m = 0; m < d; ++m) {
-                out.tau.push_back(ep.t[k] / rmin);
-                out.w.push_back(gamma * ep.c[k] * std::pow(rmin, alpha - 1.0));
+    out.r_minus = (int)out.tau.size();
+    if (g.b != 0.0) {
+        if (g.sp < 1.0) {
+            // b rho^sp = b rho * rho^(sp-1) (Lemma 4.1): d terms per node of the rho^(sp-1) sum
+            ep = exp_sum(1.0 - g.sp, B, delta, 0.5);
+            if (ep.t.empty()) return false;
+            for (size_t k = 0; k < ep.t.size(); ++k)
+                for (int m = 0; m < d; ++m) {
+                    out.tau.push_back(ep.t[k] / rmin);
+                    out.w.push_back(g.b * ep.c[k] * std::pow(rmin, g.sp - 1.0));
+                    out.mode.push_back(m);
+                }
+            out.r_plus = (int)ep.t.size();
+        } else {
+            for (int m = 0; m < d; ++m) {            // b rho = b sum_m lambda_m (rank d)
+                out.tau.push_back(0.0);
+                out.w.push_back(g.b);
                 out.mode.push_back(m);
             }
-        out.r_plus = (int)ep.t.size();
-        // accuracy on a geometric rho grid: separable sums evaluated at rho = sum of lambdas
-        double err = 0.0;
-        const int G = 2000;
-        for (int i = 0; i < G; ++i) {
-            double rho = rmin * std::pow(B, i / (G - 1.0));
-            double sm = 0.0, sp = 0.0;
-            for (size_t k = 0; k < em.t.size(); ++k) sm += em.c[k] * std::exp(-em.t[k] * rho / rmin);
-            for (size_t k = 0; k < ep.t.size(); ++k) sp += ep.c[k] * std::exp(-ep.t[k] * rho / rmin);
-            double g = beta * beta * std::pow(rmin, -alpha) * sm + gamma * rho * std::pow(rmin, alpha - 1.0) * sp;
-            err = std::max(err, std::fabs(g / g_exact(rho, alpha, beta, gamma) - 1.0));
         }
-        out.err = err;
-    } else {
-        for (int m = 0; m < d; ++m) {
-            out.tau.push_back(0.0);
-            out.w.push_back(gamma);
-            out.mode.push_back(m);
-        }
-        out.r_plus = 0;
-        double err = 0.0;
-        const int G = 2000;
-        for (int i = 0; i < G; ++i) {
-            double rho = rmin * std::pow(B, i / (G - 1.0));
+    }
+    if (g.c != 0.0) {                                // constant: exp(0 lambda) in every mode
+        out.tau.push_back(0.0);
+        out.w.push_back(g.c);
+        out.mode.push_back(-1);
+    }
+    if (out.tau.empty()) return false;
+    // accuracy on a geometric rho grid: separable sums evaluated at rho = sum of lambdas
+    double err = 0.0;
+    const int G = 2000;
+    for (int i = 0; i < G; ++i) {
+        const double rho = rmin * std::pow(B, i / (G - 1.0));
+        double v = g.c;
+        if (g.a != 0.0) {
             double sm = 0.0;
             for (size_t k = 0; k < em.t.size(); ++k) sm += em.c[k] * std::exp(-em.t[k] * rho / rmin);
-            double g = beta * beta * std::pow(rmin, -alpha) * sm + gamma * rho;
-            err = std::max(err, std::fabs(g / g_exact(rho, alpha, beta, gamma) - 1.0));
+            v += g.a * std::pow(rmin, -g.sn) * sm;
         }
-        out.err = err;
+        if (g.b != 0.0) {
+            if (g.sp < 1.0) {
+                double sp = 0.0;
+                for (size_t k = 0; k < ep.t.size(); ++k) sp += ep.c[k] * std::exp(-ep.t[k] * rho / rmin);
+                v += g.b * rho * std::pow(rmin, g.sp - 1.0) * sp;
+            } else {
+                v += g.b * rho;
+            }
+        }
+        err = std::max(err, std::fabs(v / g.eval(rho) - 1.0));
     }
+    out.err = err;
     return true;
+}
+
+bool build_inverse_power_nodes(const std::vector<double>& lam, int d, double s, double delta,
+                               SymbolNodes& out) {
+    SymbolSpec g;
+    g.a = 1.0;
+    g.sn = s;
+    return build_symbol_nodes(lam, d, g, delta, out);
 }
 
 // Least squares min ||A x - b|| (A is m x k column-major, m >= k) by Householder QR.
@@ -238,8 +261,8 @@ static bool lstsq(std::vector<double> A, int m, int k, std::vector<double> b, st
     return true;
 }
 
-bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
-                         double gamma, int rank, SymbolNodes& out) {
+bool build_precond_nodes(const std::vector<double>& lam, int d, const SymbolSpec& gs, int rank,
+                         SymbolNodes& out) {
     // Fit p(rho) = sum_k w_k exp(-tau_k rho) to 1/g(rho) by least squares of p*g - 1 on a
     // geometric grid of [rho_min, rho_max], nodes tau_k geometric in
     // [0.2/rho_max, 20/rho_min]; columns scaled to unit norm before the solve.
@@ -252,7 +275,7 @@ bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, do
     if (!(rmax > rmin * (1.0 + 1e-9))) {
         // a single eigenvalue (n = 1): the exact inverse symbol is the constant 1/g(rho_min)
         out.tau.push_back(0.0);
-        out.w.push_back(1.0 / g_exact(rmin, alpha, beta, gamma));
+        out.w.push_back(1.0 / gs.eval(rmin));
         out.mode.push_back(-1);
         out.r_minus = 1;
         out.err = 0.0;
@@ -265,7 +288,7 @@ bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, do
     const double lr0 = std::log(rmin), lr1 = std::log(rmax);
     for (int i = 0; i < G; ++i) {
         rho[i] = std::exp(lr0 + (lr1 - lr0) * i / (G - 1.0));
-        g[i] = g_exact(rho[i], alpha, beta, gamma);
+        g[i] = gs.eval(rho[i]);
     }
     std::vector<double> A((size_t)G * rank), cn(rank), b(G, 1.0), w;
     for (int k = 0; k < rank; ++k) {
@@ -334,11 +357,22 @@ bool compress_factor(const double* E, int n, int R, const double* xa, double tol
         const double s = std::fabs(xa[k]);
         for (int i = 0; i < n; ++i) X0[i + (size_t)k * n] = E[i + (size_t)k * n] * s;
     }
-    // The right singular vectors of X come from the one-sided Jacobi below; for tall X it
-    // runs on the R x R triangle of a QR factorisation (same right singular vectors).
+    // The right singular vectors come from the row-normalised D^-1 X (D = diag of the row
+    // norms): truncating its SVD relative to its largest singular value keeps every row of X
+    // (every eigenvalue index of the symbol) accurate relative to that row's own size, not to
+    // the largest row; the symbol's rows span many orders of magnitude at large n (the
+    // Lemma 4.1 terms carry lambda up to 4 (n+1)^2).  The one-sided Jacobi runs on the
+    // R x R triangle of a QR factorisation for tall X (same right singular vectors).
+    std::vector<double> Xs(X0);
+    for (int i = 0; i < n; ++i) {
+        double s2 = 0.0;
+        for (int k = 0; k < R; ++k) s2 += X0[i + (size_t)k * n] * X0[i + (size_t)k * n];
+        const double inv = (s2 > 0.0) ? 1.0 / std::sqrt(s2) : 1.0;
+        for (int k = 0; k < R; ++k) Xs[i + (size_t)k * n] *= inv;
+    }
     const bool tall = n > R;
     const int m = tall ? R : n;
-    std::vector<double> X = tall ? householder_r(X0, n, R) : X0;
+    std::vector<double> X = tall ? householder_r(Xs, n, R) : Xs;
     std::vector<double> V((size_t)R * R, 0.0), nrm(R);
     for (int k = 0; k < R; ++k) V[k + (size_t)k * R] = 1.0;
     const int n_full = n;

@@ -28,21 +28,37 @@ struct SymbolNodes {
     double rho_min = 0, rho_max = 0, err = 0;
 };
 
+// Operator symbol g(rho) = a rho^-sn + b rho^sp + c with 0 < sn <= 1, 0 < sp <= 1:
+//   control operator beta^2 A^-alpha + gamma A^alpha: a = beta^2, sn = sp = alpha, b = gamma;
+//   the test operators of Section 6 (Tables 6.1-6.4): A^alpha (a = 0, b = 1, sp = alpha) and
+//   I + A^(2 alpha) (a = 0, b = 1, sp = 2 alpha <= 1, c = 1); A^alpha + A^-alpha is the control
+//   operator at beta = gamma = 1.
+struct SymbolSpec {
+    double a = 0, sn = 1, b = 0, sp = 1, c = 0;
+    double eval(double rho) const;
+};
+
 std::vector<double> spectrum(int n);
 ExpSum exp_sum(double s, double B, double delta, double s0);
-double g_exact(double rho, double alpha, double beta, double gamma);
 // The 1D spectrum lam (ascending) is passed in: lambda_k of the Laplacian, or lambda_k^alpha
-// for the directionally fractional operator (which then uses exponent 1).
-bool build_control_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
-                         double gamma, double delta, SymbolNodes& out);
-bool build_precond_nodes(const std::vector<double>& lam, int d, double alpha, double beta,
-                         double gamma, int rank, SymbolNodes& out);
+// for the directionally fractional operator (which then uses exponent 1).  Terms in the
+// order: the rho^-sn sum (r_minus terms), the Lemma 4.1 terms of rho^sp, the constant c.
+bool build_symbol_nodes(const std::vector<double>& lam, int d, const SymbolSpec& g, double delta,
+                        SymbolNodes& out);
+// Preconditioner: least-squares exponential sum of 1/g (rank terms) ...
+bool build_precond_nodes(const std::vector<double>& lam, int d, const SymbolSpec& g, int rank,
+                         SymbolNodes& out);
+// ... or the sinc-quadrature exponential sum of rho^-s itself (the symbol g_1 = rho^-alpha of
+// Section 6, the exact inverse of A^alpha).
+bool build_inverse_power_nodes(const std::vector<double>& lam, int d, double s, double delta,
+                               SymbolNodes& out);
 
 // Compressed mode factor of a CP symbol: with X = E diag|xa| (n x R, E column-major with unit
-// columns) and its thin SVD X = U S V^T truncated to the r singular values above tol * S_max,
-//   Et = U S = X V_r  (n x r),   Mt = V_r^T diag(1/|xa|)  (r x R),
-// so that E ~ Et Mt (weighted error sqrt(sum_{i>r} s_i^2)) and Mt diag(xa^2) Mt^T = I.
-// The SVD is a one-sided (Hestenes) Jacobi on the columns of X, in FP64.
+// columns), D the diagonal of its row norms and the thin SVD D^-1 X = U S V^T truncated to the
+// r singular values above tol * S_max,
+//   Et = X V_r  (n x r),   Mt = V_r^T diag(1/|xa|)  (r x R),
+// so that E ~ Et Mt with every row of X kept to ~tol relative to its own norm, and
+// Mt diag(xa^2) Mt^T = I.  The SVD is a one-sided (Hestenes) Jacobi, in FP64.
 struct Compressed {
     int r = 0;
     std::vector<double> Et;   // n x r

@@ -1,5 +1,7 @@
-"""State recovery (eqn:State) and the directionally fractional Laplacian (Remark after
-Lemma 4.1) through the C ABI, against the CPU FP64 oracle's full-format definitions."""
+"""State recovery (eqn:State), the directionally fractional Laplacian (Remark after
+Lemma 4.1) and the test operators of Section 6 (A^alpha, I + A^(2 alpha), A^alpha + A^-alpha
+with their preconditioners) through the C ABI, against the CPU FP64 oracle's full-format
+definitions."""
 import numpy as np
 import pytest
 import torch
@@ -71,3 +73,53 @@ def test_directional_operator_solve(n, d, alpha, gamma_):
           f"CP err {e_cp:.2e} full err {e_full:.2e}")
     assert e_full < 1e-12
     assert e_cp < 1e-6
+
+
+@pytest.mark.parametrize("kind,pkind,d,n,alpha", [
+    (1, 0, 2, 255, 0.5), (1, 1, 2, 255, 0.5), (2, 0, 2, 255, 0.5), (0, 0, 2, 255, 0.5),
+    (1, 1, 3, 64, 0.5), (2, 0, 3, 64, 0.1), (0, 0, 3, 64, 0.1), (1, 0, 3, 64, 0.1)])
+def test_section6_operators_solve(kind, pkind, d, n, alpha):
+    """L u = b for the operators of Tables 6.1-6.4: A^alpha (kind 1), I + A^(2 alpha) (kind 2)
+    and A^alpha + A^-alpha (kind 0 at beta = gamma = 1), preconditioned by the least-squares
+    exponential sum of 1/g (pkind 0) or by the exponential sum of rho^-alpha (pkind 1, the
+    symbol g_1, exact for A^alpha).  CP-PCG vs the oracle's eigenbasis solve."""
+    import paper_1809_01971_gb300 as fc
+    y = fi.gaussians_cp(n, d, 3, np.random.default_rng(fi.seed_for(13, n + 10 * kind)))
+    cap = 96 if d == 2 else 192
+    h = fc.fc_setup(n, d, alpha, 1.0, 1.0, 1e-11, max_rank=cap, op_kind=kind,
+                    precond_kind=pkind)
+    U = fc.CP(d, n, cap)
+    info = fc.fc_solve(h, fc.CP.from_factors(*y), U, tol=1e-10, eps=1e-11)
+    ref = full.solve_full_op(cp.to_full(y), kind, alpha)
+    e = rel(fc.fc_to_full(h, U).cpu().numpy(), ref)
+    print(f"operator kind {kind} precond {pkind} d={d} n={n} alpha={alpha}: iters {info.iters} "
+          f"rank {U.rank} err {e:.2e} (symbol err {h.info.sym_err:.1e}, precond max|pg-1| "
+          f"{h.info.pc_err:.2f})")
+    assert info.status == 0 and e < 1e-6
+    if kind == 1 and pkind == 1 and info.max_rank_seen < cap:
+        assert info.iters <= 2          # g_1 is the exact inverse symbol of A^alpha
+    if kind != 0:                       # the state y = beta A^-alpha u needs the control operator
+        with pytest.raises(fc.FCError) as ex:
+            fc.fc_state(h, U, 1e-8, cap, fc.CP(d, n, cap))
+        assert ex.value.code == fc.fc.FC_EINVAL
+
+
+def test_section6_iterations_vs_preconditioner_rank():
+    """Trend of Table 6.1 (2D, alpha = 1/2, A^alpha + A^-alpha, residual 1e-6): PCG iterations
+    against the rank r of the exponential-sum preconditioner, r in {1, 5, 6, 10}.  The
+    paper's right-hand side is not given, so only the trend is checked: every solve
+    converges, and rank 10 needs at most the iterations of rank 1."""
+    import paper_1809_01971_gb300 as fc
+    n, d, alpha = 255, 2, 0.5
+    y = fi.gaussians_cp(n, d, 3, np.random.default_rng(fi.seed_for(14, n)))
+    ref = full.solve_full_op(cp.to_full(y), 0, alpha)
+    its = {}
+    for r in (1, 5, 6, 10):
+        h = fc.fc_setup(n, d, alpha, 1.0, 1.0, 1e-8, max_rank=64, precond_rank=r)
+        U = fc.CP(d, n, 64)
+        info = fc.fc_solve(h, fc.CP.from_factors(*y), U, tol=1e-6, eps=1e-8)
+        e = rel(fc.fc_to_full(h, U).cpu().numpy(), ref)
+        its[r] = info.iters
+        print(f"precond rank {r}: max|pg-1| {h.info.pc_err:.3f} iters {info.iters} err {e:.1e}")
+        assert info.status == 0 and e < 1e-4
+    assert its[10] <= its[1]

@@ -91,3 +91,31 @@ def test_state_is_beta_A_minus_alpha_u():
     Am = full.brute_force_power(ns, -alpha)
     ref = beta * (Am @ u.reshape(-1)).reshape(ns)
     assert np.linalg.norm(full.state_full(u, alpha, beta) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("kind,alpha", [(1, 0.5), (1, 0.1), (2, 0.5), (2, 0.1), (0, 0.5)])
+@pytest.mark.parametrize("ns", [(9, 11), (5, 6, 7)])
+def test_test_operators_match_brute_force(kind, alpha, ns):
+    """Section 6 test operators A^alpha, I + A^(2 alpha) (and A^alpha + A^-alpha = the control
+    operator at beta = gamma = 1): eigenbasis solve vs a dense eigendecomposition solve."""
+    rng = np.random.default_rng(300 + kind + len(ns))
+    b = rng.standard_normal(ns)
+    u = full.solve_full_op(b, kind, alpha)
+    ref = full.brute_force_op(b, kind, alpha)
+    assert np.linalg.norm(u - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_test_operator_symbols_special_cases():
+    """Closed forms: A^alpha at alpha = 1 is A itself (the 5-point Laplacian: rho = sum of the
+    eigenvalues); I + A^(2 alpha) at alpha = 1/2 is I + A; kind 0 at beta = gamma = 1 is
+    rho^alpha + rho^-alpha."""
+    rho = np.array([3.0, 10.0, 1e4])
+    assert np.allclose(full.g_operator(rho, 1, 1.0), rho, rtol=1e-15)
+    assert np.allclose(full.g_operator(rho, 2, 0.5), 1.0 + rho, rtol=1e-15)
+    assert np.allclose(full.g_operator(rho, 0, 0.3), rho**0.3 + rho**-0.3, rtol=1e-15)
+    # dense check: kind 1 at alpha = 1 solves with A itself
+    rng = np.random.default_rng(301)
+    b = rng.standard_normal((6, 7))
+    A = full.dense_laplacian(b.shape)
+    assert np.allclose(full.solve_full_op(b, 1, 1.0).reshape(-1), np.linalg.solve(A, b.reshape(-1)),
+                       rtol=1e-11, atol=1e-14)
