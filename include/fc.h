@@ -185,17 +185,18 @@ int fc_state(fc_handle h, const fc_cp* u, double eps, int max_rank, fc_cp* y, vo
  * Algorithm 1).  Synchronises. */
 int fc_inner(fc_handle h, const fc_cp* x, const fc_cp* y, double* out_host, void* stream);
 
-/* Algorithm 1 (low-rank PCG, Section 3.3) with X^(0) = 0 for (beta^2 A^-alpha + gamma A^alpha)
- * u = rhs; every update is truncated with fc_truncate's rule.  u->cap >= max_rank.
+/* Algorithm 1 (low-rank PCG, Section 3.3) with X^(0) = 0 for L u = rhs, L the handle's operator
+ * (beta^2 A^-alpha + gamma A^alpha unless fc_setup_opts.op_kind selects a test operator);
+ * every update is truncated with fc_truncate's rule.  u->cap >= max_rank.
  * Returns FC_OK or the failure status (also in info->status). */
 int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* opts,
              fc_solve_info* info, void* stream);
 
 /* `count` independent solves (each as fc_solve on its own handle, right-hand side rhs[i],
- * solution u[i], options opts[i] (opts may be NULL), info[i]), run concurrently: one host
- * thread per problem drives Algorithm 1 on streams[i].  A single solve keeps only a few of
- * the 152 SMs busy (its small FP64 eigen-solves run on one CTA each), so independent problems
- * overlap on the device.  Handles and streams must be pairwise distinct (FC_EINVAL otherwise);
+ * solution u[i], options opts[i] (opts may be NULL), info[i]), run concurrently: a pool of at
+ * most 16 host threads takes the problems in order, each driving Algorithm 1 on streams[i].
+ * A single solve keeps only a few of the 152 SMs busy (its small eigen-solves run on one CTA
+ * each), so independent problems overlap on the device.  Handles and streams must be pairwise distinct (FC_EINVAL otherwise);
  * the calling thread's current device is used.  Returns FC_OK if every solve returned FC_OK,
  * else the first failing problem's code; info[i].status holds each problem's own status. */
 int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
@@ -205,7 +206,8 @@ int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
 int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream);
 
 /* Full-format eigenbasis solve u = (F x..x F) diag(1/g(rho)) (F x..x F) rhs with the exact
- * symbol g(rho) = beta^2 rho^-alpha + gamma rho^alpha (eqn:DiagFLaplace3D, Section 3.2);
+ * symbol of the handle's operator, g(rho) = beta^2 rho^-alpha + gamma rho^alpha for the control
+ * operator (eqn:DiagFLaplace3D, Section 3.2);
  * rhs and u are n^d column-major device arrays (may alias). Needs n^d doubles of workspace
  * beyond fc_workspace_size: pass it as dev_tmp. */
 int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev_tmp,

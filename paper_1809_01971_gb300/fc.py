@@ -306,7 +306,8 @@ def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
 
 def fc_solve_batched(handles, rhs, us, streams, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
                      raise_on_fail: bool = True):
-    """Independent solves run concurrently (one host thread and one stream per problem).
+    """Independent solves run concurrently (a pool of up to 16 host threads, one stream per
+    problem).
     tol / eps / kmax / max_rank are scalars or per-problem sequences."""
     count = len(handles)
 

@@ -327,3 +327,35 @@ def test_solve_batched_matches_independent_solves(fc):
         assert rel(ub, us) <= 2.0 * max(rel(ub, ref), rel(us, ref)) + 1e-12
     with pytest.raises(fc.FCError):
         fc.fc_solve_batched([hs[0], hs[0]], Bs[:2], Ub[:2], streams[:2])
+
+
+def test_batched_mixed_problems(fc):
+    """Batching form with uneven problems: 3D n in {127, 255, 511}, alpha ~ U[0.1, 0.9], gamma
+    log-uniform in [1e-4, 1], rank 1-8 Gaussians, tol 1e-6, eps 1e-7 (the mixed-batch recipe),
+    more problems than the worker pool has threads, tensor-core form.  Every solution against
+    the library's full-format eigenbasis solve."""
+    probs = [p for p in (fi.config4(i) for i in range(80)) if p.n <= 511][:20]
+    hs = [fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank,
+                      precision=2) for p in probs]
+    Bs = [fc.CP.from_factors(*p.rhs()) for p in probs]
+    Us = [fc.CP(p.d, p.n, p.max_rank) for p in probs]
+    streams = [torch.cuda.Stream() for _ in probs]
+    infos = fc.fc_solve_batched(hs, Bs, Us, streams, tol=[p.tol for p in probs],
+                                eps=[p.eps for p in probs], raise_on_fail=False)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for p, h, B, U, info in zip(probs, hs, Bs, Us, infos):
+        n3 = p.n ** 3
+        b = torch.empty(n3, dtype=torch.float64, device="cuda")
+        fc.fc_to_full(h, B, out=b)
+        u = torch.empty_like(b)
+        tmp = torch.empty_like(b)
+        fc.fc_full_solve(h, b, u, tmp)
+        got = b                                  # reuse: column-major n^3 of the CP solution
+        fc.fc_to_full(h, U, out=got)
+        e = float(torch.linalg.norm(got - u) / torch.linalg.norm(u))
+        worst = max(worst, e)
+        print(f"{p.label} status {info.status} rank {U.rank} iters {info.iters} err {e:.1e}")
+        assert info.status == 0 and e < 2e-5
+        del b, u, tmp, got
+    print(f"{len(probs)} mixed problems, worst error {worst:.1e}")
