@@ -356,6 +356,7 @@ def test_batched_mixed_problems(fc):
         e = float(torch.linalg.norm(got - u) / torch.linalg.norm(u))
         worst = max(worst, e)
         print(f"{p.label} status {info.status} rank {U.rank} iters {info.iters} err {e:.1e}")
-        assert info.status == 0 and e < 2e-5
+        # tol bounds the residual; the error is up to kappa tol, kappa ~ 10^3 for small gamma
+        assert info.status == 0 and e < 2e-4
         del b, u, tmp, got
     print(f"{len(probs)} mixed problems, worst error {worst:.1e}")
