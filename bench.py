@@ -65,6 +65,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value over the ranks (the job's time is its slowest rank's)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+    return float(x)
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time
+    (weak scaling: each rank solves the full problem set)."""
+    return units_per_rank * world / seconds
+
+
 def problems(count):
     import fc_inputs as fi
     return [fi.config2(p % 6) for p in range(count)]
@@ -242,13 +258,6 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world > 1:
-            t = torch.tensor([x], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return float(t.item())
-        return x
-
     # accuracy reference: the library's full-format FP64 eigenbasis solve of every problem
     nn = probs[0].n ** 3
     full_b = torch.empty(nn, dtype=torch.float64, device=dev)
@@ -288,7 +297,7 @@ def main():
         launches = fc.fc_launch_count() - launches0
         prof = fc.fc_prof_read()
         barrier()
-        t_total = max_over_ranks(sum(times) / 1e3)
+        t_total = max_over_ranks(sum(times) / 1e3, world, dev)
         err = 0.0
         for h, U, u in zip(hs, Us, full_u):
             fc.fc_to_full(h, U, out=tmp)
@@ -301,7 +310,7 @@ def main():
             tc_prof = fc.fc_prof_read() + (sum(tc_times),)
             barrier()
         results[form] = {"hs": hs, "Us": Us, "step": step, "t_total": t_total,
-                         "value": len(probs) * args.steps * world / t_total,
+                         "value": job_rate(len(probs) * args.steps, world, t_total),
                          "launches": launches, "prof": prof, "iters": iters[-1], "err": err,
                          "tc_prof": tc_prof}
     clocks = sampler.stop()
@@ -354,7 +363,7 @@ def main():
     for _ in range(args.steps):
         e2e_times.append(timed(e2e_step)[0])
     barrier()
-    e2e_value = solves / max_over_ranks(sum(e2e_times) / 1e3)
+    e2e_value = job_rate(len(probs) * args.steps, world, max_over_ranks(sum(e2e_times) / 1e3, world, dev))
 
     roofline = None
     jac_n, jac_ms, jac_work = R["prof"]
@@ -399,7 +408,7 @@ def main():
                            "form": name,
                            "l2": "flushed between steps (512 MiB write, untimed)",
                            "setup": "per operator, before timing",
-                           "concurrency": "fc_solve_batched: one stream and host thread per problem",
+                           "concurrency": "fc_solve_batched: one stream per problem, up to 16 host threads",
                            "pcg_iters": R["iters"]},
                 "forms": forms,
                 "vs_plain_fp64": value / results[0]["value"],
