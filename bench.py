@@ -9,10 +9,11 @@ preconditioner CP factors, workspace) is done once before timing, as a library u
 would for repeated solves with one operator; the timed step is the full Algorithm 1
 (PCG with RHOSVD truncation) for all six right-hand sides.
 
-The step runs in each of the three contraction forms of the library (fc_setup precision
-0: FP64; 1: double-float FP32; 2: FP64-accurate digit products on the BF16 tensor cores);
-`forms` reports all three, and `value` is the fastest form whose solutions are all within
-1e-6 of the exact one (`config.form`), `vs_plain_fp64` its ratio to the FP64 form.
+The step runs in each contraction form of the library (fc_setup precision 0: FP64; 1:
+double-float FP32; 2: FP64-accurate digit products on the BF16 tensor cores), and form 2 also
+with the spectral-resident iteration (fc_solve_opts.spectral); `forms` reports all of them,
+and `value` is the fastest whose solutions are all within 1e-6 of the exact one
+(`config.form`), `vs_plain_fp64` its ratio to the FP64 form.
 
 `value`  : device-resident solves/s (CUDA events on the launching stream, L2 flushed
            between steps with a 512 MiB write, outside the events).
@@ -204,11 +205,14 @@ TC_TRAFFIC_BYTES = None
 EIG_TRAFFIC_BYTES = None
 
 
-FORMS = {0: ("fp64", "f64", "FP64 throughout"),
-         1: ("df32", "f32x2", "large contractions in double-float FP32 (hi+lo); rest FP64"),
-         2: ("tc64", "bf16-digits/f64", "large contractions as exact products of 8 fixed-point "
-                                        "7-bit digits on the BF16 tensor cores (tcgen05, FP32 "
-                                        "TMEM accumulation, FP64-level error); rest FP64")}
+# (name, fc_setup precision, spectral-resident iteration, dtype, contractions)
+FORMS = [("fp64", 0, False, "f64", "FP64 throughout"),
+         ("df32", 1, False, "f32x2", "large contractions in double-float FP32 (hi+lo); rest FP64"),
+         ("tc64", 2, False, "bf16-digits/f64",
+          "large contractions as exact products of 8 fixed-point 7-bit digits on the BF16 "
+          "tensor cores (tcgen05, FP32 TMEM accumulation, FP64-level error); rest FP64"),
+         ("tc64_spectral", 2, True, "bf16-digits/f64",
+          "as tc64, iterates kept in the DST-I eigenbasis (one transform at entry and exit)")]
 
 
 def main():
@@ -274,15 +278,18 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     results = {}
-    for form in (0, 1, 2):
-        hs = href if form == 0 else [
-            fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank,
-                        precision=form) for p in probs]
+    handles = {0: href}
+    for form, (fname, prec, spectral, _, _) in enumerate(FORMS):
+        if prec not in handles:
+            handles[prec] = [fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps,
+                                         max_rank=p.max_rank, precision=prec) for p in probs]
+        hs = handles[prec]
         Us = [fc.CP(p.d, p.n, p.max_rank, device=dev) for p in probs]
 
-        def step(hs=hs, Us=Us):
+        def step(hs=hs, Us=Us, spectral=spectral):
             # the step's problems run concurrently, one stream each (fc_solve_batched)
-            return fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss)
+            return fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss,
+                                       spectral=spectral)
 
         for _ in range(args.warmup):
             step()
@@ -303,7 +310,7 @@ def main():
             fc.fc_to_full(h, U, out=tmp)
             err = max(err, float(torch.linalg.norm(tmp - u) / torch.linalg.norm(u)))
         tc_prof = None
-        if form == 2:
+        if fname == "tc64":
             # the tensor-core contraction class, instrumented over extra (untimed) steps
             fc.fc_prof_enable(fc.fc.PROF_TC)
             tc_times = [timed(step)[0] for _ in range(args.steps)]
@@ -351,7 +358,7 @@ def main():
                 B.xi[:R_].copy_(xi_h, non_blocking=True)
                 B.U[:, :R_, :p.n].copy_(U_h, non_blocking=True)
             B.rank = R_
-        fc.fc_solve_batched(hsb, Bs, Usb, streams, tol=tols, eps=epss)
+        fc.fc_solve_batched(hsb, Bs, Usb, streams, tol=tols, eps=epss, spectral=FORMS[best][2])
         for (xo, Uo), p, U, s_ in zip(host_out, probs, Usb, streams):
             with torch.cuda.stream(s_):
                 xo.copy_(U.xi[:p.max_rank], non_blocking=True)
@@ -380,7 +387,7 @@ def main():
                     "event_ms_over_step_ms": jac_ms / (t_total * 1e3),
                     "note": "launches overlap across the problem streams, so summed event time can exceed step time"}
     roofline_tc = None
-    if results[2]["tc_prof"] and results[2]["tc_prof"][0] > 0:
+    if results[2]["tc_prof"] and results[2]["tc_prof"][0] > 0:    # FORMS[2] = tc64
         tn, tms, twork, tstep_ms = results[2]["tc_prof"]
         achieved = twork / tn / (tms / tn * 1e-3) / 1e12
         peak = BF16_PEAK_SUSTAINED_TFLOPS
@@ -393,13 +400,13 @@ def main():
                        "launches": tn, "avg_launch_us": 1e3 * tms / tn,
                        "event_ms_over_step_ms": tms / tstep_ms}
     if rank == 0:
-        name, dtype, what = FORMS[best]
+        name, _, _, dtype, what = FORMS[best]
         forms = {FORMS[f][0]: {"value": results[f]["value"], "unit": UNIT,
                                "ms_per_step": 1e3 * results[f]["t_total"] / args.steps,
                                "max_rel_err_vs_full": results[f]["err"],
                                "pcg_iters": results[f]["iters"],
                                "gpu_launches": int(results[f]["launches"]),
-                               "contractions": FORMS[f][2]} for f in results}
+                               "contractions": FORMS[f][4]} for f in results}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,

@@ -108,6 +108,11 @@ typedef struct fc_solve_opts {
     double eps;         /* truncation accuracy; <= 0 means the eps given to fc_setup         */
     int kmax;           /* iteration limit [100]                                              */
     int max_rank;       /* CP rank cap of the iterates; <= 0 means the fc_setup value         */
+    int spectral;       /* != 0: spectral-resident iteration: B is transformed once (DST-I of  */
+                        /* its factors), every iterate stays in the eigenbasis where symbol    */
+                        /* and preconditioner are diagonal and inner products are unchanged    */
+                        /* (F orthogonal), and X is transformed back once at exit; the same    */
+                        /* result without the two DSTs per mat-vec [0]                          */
 } fc_solve_opts;
 
 typedef struct fc_solve_info {

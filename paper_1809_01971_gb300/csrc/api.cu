@@ -117,6 +117,7 @@ struct fc_ctx {
     double *xiS = nullptr, *GES = nullptr;
     int RS = 0;
     SymbolSpec spec;      // operator symbol g(rho) = a rho^-sn + b rho^sp + c
+    bool spectral = false;   // during a spectral-resident solve: operands already in the eigenbasis
     double alpha_eff = 0.0;   // exponent of the symbol's spectrum (1 for the directional operator)
     int prec = GP_F64;        // contractions in FP64 or double-float FP32 (fc_setup_opts.precision)
     // compressed mode factors of the three symbols (operator, preconditioner, state):
@@ -518,7 +519,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     CKL();
     // ---- output factors U'_l = Z_l X_l (eigen-index domain: F (Z_l X_l)) ------------------
     const double* Zuse = w.Z;
-    if (kr) {
+    if (kr && !h->spectral) {
         const double* in[3] = {w.Z, w.Z + nC, w.Z + 2 * nC};
         double* o[3] = {w.Zr, w.Zr + nC, w.Zr + 2 * nC};
         dst_cols(h, st, rz, in, n, o, n);
@@ -548,7 +549,14 @@ int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, int which, KRIn& kr) {
     const long long nK = (long long)h->n * h->KIN;
     const double* in[3] = {x.U[0], x.U[1], x.U[2]};
     double* o[3] = {h->w.Yh, h->w.Yh + nK, h->w.Yh + 2 * nK};
-    dst_cols(h, st, x.rank, in, x.ld, o, h->n);
+    if (h->spectral) {                    // already in the eigenbasis: copy the factors
+        for (int l = 0; l < h->d; ++l)
+            if (x.rank > 0)
+                CK(cudaMemcpy2DAsync(o[l], sizeof(double) * h->n, in[l], sizeof(double) * x.ld,
+                                     sizeof(double) * h->n, x.rank, cudaMemcpyDeviceToDevice, st));
+    } else {
+        dst_cols(h, st, x.rank, in, x.ld, o, h->n);
+    }
     if (which == 1) {
         kr.xa = h->xiP; kr.E = h->EP; kr.Ra = h->RP; kr.bsE = (long long)h->n * h->RP; kr.GE = h->GEP;
     } else if (which == 2) {
@@ -996,7 +1004,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
              fc_solve_info* info, void* stream) {
     if (!h || !check_cp(h, rhs, false) || !check_cp(h, u, true)) return FC_EINVAL;
     if (!h->ws) return FC_EWORKSPACE;
-    fc_solve_opts opts{1e-8, 0.0, 100, 0};
+    fc_solve_opts opts{1e-8, 0.0, 100, 0, 0};
     if (o) opts = *o;
     if (!(opts.tol > 0.0)) opts.tol = 1e-8;
     if (opts.kmax <= 0) opts.kmax = 100;
@@ -1024,11 +1032,17 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         inf.tucker_max = h->stat_rmax;
         inf.basis_max = h->stat_bmax;
         inf.tucker_mean = h->stat_rcount ? (double)h->stat_rsum / h->stat_rcount : 0.0;
-        // copy X to the caller's u
-        for (int l = 0; l < h->d; ++l)
-            if (X.rank > 0)
-                CK(cudaMemcpy2DAsync(u->U[l], sizeof(double) * u->ld, X.U[l], sizeof(double) * X.ld,
-                                     sizeof(double) * h->n, X.rank, cudaMemcpyDeviceToDevice, st));
+        // X to the caller's u (spectral-resident: transformed back from the eigenbasis)
+        if (h->spectral && X.rank > 0) {
+            const double* xin[3] = {X.U[0], X.U[1], X.U[2]};
+            double* uo[3] = {u->U[0], u->U[1], u->U[2]};
+            dst_cols(h, st, X.rank, xin, X.ld, uo, u->ld);
+        } else {
+            for (int l = 0; l < h->d; ++l)
+                if (X.rank > 0)
+                    CK(cudaMemcpy2DAsync(u->U[l], sizeof(double) * u->ld, X.U[l], sizeof(double) * X.ld,
+                                         sizeof(double) * h->n, X.rank, cudaMemcpyDeviceToDevice, st));
+        }
         if (X.rank > 0) launch_copy_weights(st, X.rank, X.xi, bscale, u->xi);   // undo 1/||B||
         u->rank = X.rank;
         CK(cudaStreamSynchronize(st));
@@ -1047,7 +1061,22 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         launch_concat_normalize(st, h->d, h->n, p0, p1, R.U[0], R.ld, R.bs(), R.xi);
         CKL();
         R.rank = B.rank;
+        if (opts.spectral && R.rank > 0) {
+            // spectral-resident iteration: R0 in the eigenbasis (unit columns stay unit)
+            const long long nK = (long long)h->n * h->KIN;
+            const double* rin[3] = {R.U[0], R.U[1], R.U[2]};
+            double* tmp[3] = {w.Yh, w.Yh + nK, w.Yh + 2 * nK};
+            dst_cols(h, st, R.rank, rin, R.ld, tmp, h->n);
+            for (int l = 0; l < h->d; ++l)
+                CK(cudaMemcpy2DAsync(R.U[l], sizeof(double) * R.ld, tmp[l], sizeof(double) * h->n,
+                                     sizeof(double) * h->n, R.rank, cudaMemcpyDeviceToDevice, st));
+        }
     }
+    h->spectral = opts.spectral != 0;
+    struct SpectralReset {
+        fc_ctx* h;
+        ~SpectralReset() { h->spectral = false; }
+    } spectral_reset{h};
     auto track = [&](const CP& c) { inf.max_rank_seen = std::max(inf.max_rank_seen, c.rank); ++inf.trunc_calls; };
     if ((rc = kr_trunc(h, st, R, 1, eps, cap, Z))) return rc;           // Z0 = trunc(precond(R0))
     track(Z);

@@ -56,7 +56,7 @@ class fc_setup_info(C.Structure):
 
 class fc_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("eps", C.c_double), ("kmax", C.c_int),
-                ("max_rank", C.c_int)]
+                ("max_rank", C.c_int), ("spectral", C.c_int)]
 
 
 class fc_solve_info(C.Structure):
@@ -293,8 +293,10 @@ def fc_inner(h: Handle, x: CP, y: CP, stream=None) -> float:
 
 
 def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0, stream=None,
-             raise_on_fail: bool = True) -> fc_solve_info:
-    o = fc_solve_opts(float(tol), float(eps), int(kmax), int(max_rank))
+             raise_on_fail: bool = True, spectral: bool = False) -> fc_solve_info:
+    """Algorithm 1; spectral=True keeps every iterate in the DST-I eigenbasis (one transform
+    at entry and exit instead of two per mat-vec: the same result)."""
+    o = fc_solve_opts(float(tol), float(eps), int(kmax), int(max_rank), 1 if spectral else 0)
     info = fc_solve_info()
     cr, cu = rhs.desc(), u.desc()
     rc = lib().fc_solve(h.ptr, C.byref(cr), C.byref(cu), C.byref(o), C.byref(info), _stream(stream))
@@ -305,7 +307,7 @@ def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
 
 
 def fc_solve_batched(handles, rhs, us, streams, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
-                     raise_on_fail: bool = True):
+                     raise_on_fail: bool = True, spectral: bool = False):
     """Independent solves run concurrently (a pool of up to 16 host threads, one stream per
     problem).
     tol / eps / kmax / max_rank are scalars or per-problem sequences."""
@@ -319,7 +321,8 @@ def fc_solve_batched(handles, rhs, us, streams, tol=1e-8, eps=0.0, kmax=100, max
     R = (fc_cp * count)(*[x.desc() for x in rhs])
     Uc = (fc_cp * count)(*[x.desc() for x in us])
     O = (fc_solve_opts * count)(*[fc_solve_opts(float(tols[i]), float(epss[i]), int(kms[i]),
-                                                int(mrs[i])) for i in range(count)])
+                                                int(mrs[i]), 1 if spectral else 0)
+                                  for i in range(count)])
     infos = (fc_solve_info * count)()
     S = (C.c_void_p * count)(*[_stream(s) for s in streams])
     rc = lib().fc_solve_batched(count, H, R, Uc, O, infos, S)

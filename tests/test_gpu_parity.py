@@ -360,3 +360,32 @@ def test_batched_mixed_problems(fc):
         assert info.status == 0 and e < 2e-4
         del b, u, tmp, got
     print(f"{len(probs)} mixed problems, worst error {worst:.1e}")
+
+
+@pytest.mark.parametrize("problem,precision", [(5, 2), (0, 0)])
+def test_spectral_resident_solve_matches(fc, problem, precision):
+    """The spectral-resident iteration (iterates in the DST-I eigenbasis, one transform at
+    entry and exit) reaches the same solution as the per-step path: both against the
+    full-format oracle, and against each other."""
+    prob = fi.config2(problem)
+    h = fc.fc_setup(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, prob.eps,
+                    max_rank=prob.max_rank, precision=precision)
+    B = fc.CP.from_factors(*prob.rhs())
+    ref = full.solve_full(cp.to_full(prob.rhs()), prob.alpha, prob.beta, prob.gamma)
+    out = {}
+    for spectral in (False, True):
+        U = fc.CP(prob.d, prob.n, prob.max_rank)
+        fc.fc_solve(h, B, U, tol=prob.tol, eps=prob.eps, spectral=spectral)   # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = fc.fc_solve(h, B, U, tol=prob.tol, eps=prob.eps, spectral=spectral)
+        e1.record()
+        e1.synchronize()
+        got = gpu_full(fc, h, U)
+        out[spectral] = got
+        e = rel(got, ref)
+        print(f"{prob.label} prec={precision} spectral={spectral}: iters {info.iters} "
+              f"rank {U.rank} err {e:.2e} {e0.elapsed_time(e1):.1f} ms")
+        assert info.status == 0 and e < 1e-6
+    assert rel(out[True], out[False]) < 1e-6
