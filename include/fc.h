@@ -89,6 +89,12 @@ typedef struct fc_setup_opts {
     int precond_kind;   /* 0: least-squares exponential sum of 1/g (rank precond_rank);       */
                         /* 1: the sinc-quadrature sum of rho^-alpha (the symbol g_1 of        */
                         /* Section 6, the exact inverse of A^alpha) [0]                        */
+    const double* coeff[3]; /* host, per mode NULL (constant 1) or n+1 values a_l((i+1/2) h),   */
+                        /* i = 0..n, all > 0: the mode-l operator is the stiffness matrix of   */
+                        /* -(a_l u')' (Remark on variable coefficients), whose orthonormal     */
+                        /* eigenvectors (implicit-QR tridiagonal eigen-solve at setup, O(n^3)) */
+                        /* replace the DST-I of that mode and whose eigenvalues the spectrum   */
+                        /* [NULL]                                                              */
 } fc_setup_opts;
 
 typedef struct fc_setup_info {

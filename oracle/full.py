@@ -8,6 +8,9 @@ brute_force: dense A = sum_l I x A_(l) x I (eqn_low_rank_lap), symmetric
              (eqn:frac_Oper), dense solve.  Independent of the DST; n <= 16.
 g_operator / solve_full_op / brute_force_op: the same for the test operators of Section 6
              (Tables 6.1-6.4): A^alpha and I + A^(2 alpha), besides the control operator.
+stiffness_1d / solve_full_varcoef / brute_force_varcoef: separable variable coefficients
+             (Remark on generalised directionally fractional operators): mode l carries the
+             stiffness matrix of -(a_l u')', its orthonormal eigenvectors replace the DST-I.
 """
 from __future__ import annotations
 
@@ -132,4 +135,61 @@ def brute_force_op(b: np.ndarray, kind, alpha, beta=1.0, gamma_=1.0) -> np.ndarr
         f = 1.0 + w ** (2.0 * alpha)
     else:
         raise ValueError(kind)
+    return np.linalg.solve(V @ np.diag(f) @ V.T, b.reshape(-1)).reshape(b.shape)
+
+
+def stiffness_1d(n: int, a_half) -> np.ndarray:
+    """Dense 1D stiffness matrix of -(a u')' with Dirichlet ends: a_half[i] = a((i+1/2) h),
+    i = 0..n; row i: (a_half[i] + a_half[i+1]) / h^2 on the diagonal, -a_half[i+1] / h^2 next
+    to it.  a = 1 gives A_(l)."""
+    a = np.asarray(a_half, dtype=np.float64)
+    h2 = (n + 1.0) ** 2
+    T = np.diag((a[:-1] + a[1:]) * h2)
+    off = -a[1:-1] * h2
+    return T + np.diag(off, 1) + np.diag(off, -1)
+
+
+def _mode_bases(shape, coeffs):
+    """Per mode: eigenvalues (ascending) and orthonormal eigenvectors of the 1D operator."""
+    out = []
+    for l, m in enumerate(shape):
+        a = coeffs[l] if coeffs is not None and l < len(coeffs) else None
+        if a is None:
+            out.append((eigenvalues(m), None))
+        else:
+            w, V = np.linalg.eigh(stiffness_1d(m, a))
+            out.append((w, V))
+    return out
+
+
+def solve_full_varcoef(b: np.ndarray, coeffs, kind, alpha, beta=1.0, gamma_=1.0) -> np.ndarray:
+    """Exact solution of L u = b for the operator of `kind` built on A = sum_l I x A_l x I,
+    A_l the stiffness matrix of mode l (DST-I for a constant coefficient): transform every
+    mode to its eigenbasis, divide by g(sum_l lambda_l), transform back."""
+    bases = _mode_bases(b.shape, coeffs)
+    Y = b.copy()
+    for l, (w, V) in enumerate(bases):
+        Y = dst1(Y, axis=l) if V is None else np.moveaxis(np.tensordot(V.T, Y, axes=(1, l)), 0, l)
+    Y = Y / g_operator(rho_full([w for w, _ in bases]), kind, alpha, beta, gamma_)
+    for l, (w, V) in enumerate(bases):
+        Y = dst1(Y, axis=l) if V is None else np.moveaxis(np.tensordot(V, Y, axes=(1, l)), 0, l)
+    return Y
+
+
+def brute_force_varcoef(b: np.ndarray, coeffs, kind, alpha, beta=1.0, gamma_=1.0) -> np.ndarray:
+    """Dense solve: A = sum_l I x A_l x I assembled from the dense 1D matrices, the operator
+    from A's eigendecomposition (no per-mode transform involved)."""
+    ns = b.shape
+    N = int(np.prod(ns))
+    A = np.zeros((N, N))
+    for l in range(len(ns)):
+        a = coeffs[l] if coeffs is not None and l < len(coeffs) else None
+        mats = [np.eye(m) for m in ns]
+        mats[l] = laplacian_1d(ns[l]) if a is None else stiffness_1d(ns[l], a)
+        K = mats[0]
+        for Mx in mats[1:]:
+            K = np.kron(K, Mx)
+        A += K
+    w, V = np.linalg.eigh(A)
+    f = g_operator(w, kind, alpha, beta, gamma_)
     return np.linalg.solve(V @ np.diag(f) @ V.T, b.reshape(-1)).reshape(b.shape)

@@ -118,6 +118,8 @@ struct fc_ctx {
     int RS = 0;
     SymbolSpec spec;      // operator symbol g(rho) = a rho^-sn + b rho^sp + c
     bool spectral = false;   // during a spectral-resident solve: operands already in the eigenbasis
+    double* V = nullptr;     // variable coefficients: orthonormal eigenvector matrices of the 1D
+                             // stiffness matrices (d x n x n, column-major), else the DST-I
     double alpha_eff = 0.0;   // exponent of the symbol's spectrum (1 for the directional operator)
     int prec = GP_F64;        // contractions in FP64 or double-float FP32 (fc_setup_opts.precision)
     // compressed mode factors of the three symbols (operator, preconditioner, state):
@@ -301,11 +303,22 @@ bool check_cp(const fc_ctx* h, const fc_cp* x, bool output) {
 
 // DST-I of `cols` columns of every mode: out_l = F in_l (Section 3.2, F = F^T = F^{-1})
 void dst_cols(fc_ctx* h, cudaStream_t st, int cols, const double* const in[3], int ldi,
-              double* const out[3], int ldo) {
+              double* const out[3], int ldo, bool forward) {
     if (cols <= 0) return;
-    LdSine F{h->sintab, 2 * (h->n + 1)};
+    const int n = h->n;
+    if (h->V) {             // per-mode eigenbases: forward V_l^T x, inverse V_l x
+        for (int l = 0; l < h->d; ++l) {
+            const double* Vl = h->V + (long long)l * n * n;
+            if (forward)
+                gemm_p(h->prec, st, n, cols, n, LdT{Vl, n, 0}, LdN{in[l], ldi, 0}, 1.0, 0.0, out[l], ldo);
+            else
+                gemm_p(h->prec, st, n, cols, n, LdN{Vl, n, 0}, LdN{in[l], ldi, 0}, 1.0, 0.0, out[l], ldo);
+        }
+        return;
+    }
+    LdSine F{h->sintab, 2 * (n + 1)};
     for (int l = 0; l < h->d; ++l)
-        gemm_p(h->prec, st, h->n, cols, h->n, F, LdN{in[l], ldi, 0}, 1.0, 0.0, out[l], ldo);
+        gemm_p(h->prec, st, n, cols, n, F, LdN{in[l], ldi, 0}, 1.0, 0.0, out[l], ldo);
 }
 
 struct KRIn {           // implicit Khatri-Rao tensor sum_{k,j} xa_k xb_j (x)_l E_l[:,k].Yh_l[:,j]
@@ -522,7 +535,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     if (kr && !h->spectral) {
         const double* in[3] = {w.Z, w.Z + nC, w.Z + 2 * nC};
         double* o[3] = {w.Zr, w.Zr + nC, w.Zr + 2 * nC};
-        dst_cols(h, st, rz, in, n, o, n);
+        dst_cols(h, st, rz, in, n, o, n, false);
         Zuse = w.Zr;
     }
     for (int l = 0; l < d; ++l)
@@ -555,7 +568,7 @@ int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, int which, KRIn& kr) {
                 CK(cudaMemcpy2DAsync(o[l], sizeof(double) * h->n, in[l], sizeof(double) * x.ld,
                                      sizeof(double) * h->n, x.rank, cudaMemcpyDeviceToDevice, st));
     } else {
-        dst_cols(h, st, x.rank, in, x.ld, o, h->n);
+        dst_cols(h, st, x.rank, in, x.ld, o, h->n, true);
     }
     if (which == 1) {
         kr.xa = h->xiP; kr.E = h->EP; kr.Ra = h->RP; kr.bsE = (long long)h->n * h->RP; kr.GE = h->GEP;
@@ -755,11 +768,45 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     // Directionally fractional operator sum_l (-Delta_l)^alpha (Remark after Lemma 4.1): the
     // same eigenbasis with eigenvalues sum_l lambda^alpha, i.e. spectrum lambda^alpha and
     // exponent 1 in g = beta^2 rho^-1 + gamma rho.
-    std::vector<double> lam = spectrum(n);
+    // Per-mode spectra: the closed-form DST-I eigenvalues, or for a mode with a coefficient
+    // a_l (Remark on variable coefficients) the eigen-decomposition of its 1D stiffness matrix
+    // of -(a_l u')', whose orthonormal eigenvectors replace the DST-I of that mode.
+    bool varcoef = false;
+    if (o)
+        for (int l = 0; l < d; ++l) varcoef |= (o->coeff[l] != nullptr);
+    std::vector<double> lam((size_t)3 * n, 0.0), Vh;
+    if (varcoef) Vh.assign((size_t)3 * n * n, 0.0);
+    {
+        const std::vector<double> lam0 = spectrum(n);
+        const double N1 = n + 1.0, sc = std::sqrt(2.0 / N1);
+        for (int l = 0; l < d; ++l) {
+            if (varcoef && o->coeff[l]) {
+                for (int i = 0; i <= n; ++i)
+                    if (!(o->coeff[l][i] > 0.0) || !std::isfinite(o->coeff[l][i])) return FC_EINVAL;
+                std::vector<double> dg, off, lv, Vl;
+                stiffness_1d(n, o->coeff[l], dg, off);
+                if (!tridiag_eig(n, dg, off, lv, Vl)) return FC_ESETUP;
+                std::copy(lv.begin(), lv.end(), lam.begin() + (size_t)l * n);
+                std::copy(Vl.begin(), Vl.end(), Vh.begin() + (size_t)l * n * n);
+            } else {
+                std::copy(lam0.begin(), lam0.end(), lam.begin() + (size_t)l * n);
+                if (varcoef)                       // this mode keeps the DST-I, stored explicitly
+                    for (int k = 0; k < n; ++k)
+                        for (int i = 0; i < n; ++i)
+                            Vh[(size_t)l * n * n + i + (size_t)k * n] =
+                                sc * std::sin(M_PI * (i + 1.0) * (k + 1.0) / N1);
+            }
+        }
+    }
     double alpha_eff = alpha;
     if (opts.directional) {
         for (double& x : lam) x = std::pow(x, alpha);
         alpha_eff = 1.0;
+    }
+    double rmin = 0.0, rmax = 0.0;               // range of rho = sum_l lambda_{i_l, l}
+    for (int l = 0; l < d; ++l) {
+        rmin += lam[(size_t)l * n];
+        rmax += lam[(size_t)l * n + n - 1];
     }
     // operator symbol: the control operator, or a test operator of Section 6
     SymbolSpec gs;
@@ -772,10 +819,10 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         gs.b = 1.0; gs.sp = 2.0 * alpha_eff; gs.c = 1.0;
     }
     SymbolNodes sym, pc;
-    if (!build_symbol_nodes(lam, d, gs, opts.delta_sym, sym)) return FC_ESETUP;
+    if (!build_symbol_nodes(rmin, rmax, d, gs, opts.delta_sym, sym)) return FC_ESETUP;
     if (opts.precond_kind == 1) {
-        if (!build_inverse_power_nodes(lam, d, alpha_eff, opts.delta_sym, pc)) return FC_ESETUP;
-    } else if (!build_precond_nodes(lam, d, gs, opts.precond_rank, pc)) {
+        if (!build_inverse_power_nodes(rmin, rmax, d, alpha_eff, opts.delta_sym, pc)) return FC_ESETUP;
+    } else if (!build_precond_nodes(rmin, rmax, gs, opts.precond_rank, pc)) {
         return FC_ESETUP;
     }
     fc_ctx* h = new (std::nothrow) fc_ctx();
@@ -797,15 +844,17 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     // device tables
     const int N = n + 1;
     const int RAm = std::max(h->RA, h->RP);
-    size_t tcount = (size_t)n + 2 * N + h->RA + h->RP + h->RS + 2 * 3 * (size_t)n * RAm +
+    size_t tcount = 3 * (size_t)n + 2 * N + h->RA + h->RP + h->RS + 2 * 3 * (size_t)n * RAm +
+                    (varcoef ? 3 * (size_t)n * n : 0) +
                     3 * 3 * (size_t)n * n;
     if (cudaMalloc(&h->tables, tcount * sizeof(double)) != cudaSuccess) {
         delete h;
         return FC_ECUDA;
     }
     double* p = h->tables;
-    h->lam = p; p += n;
+    h->lam = p; p += 3 * (size_t)n;
     h->sintab = p; p += 2 * N;
+    if (varcoef) { h->V = p; p += 3 * (size_t)n * n; }
     h->xiA = p; p += h->RA;
     h->xiP = p; p += h->RP;
     h->EA = p; p += 3 * (size_t)n * RAm;
@@ -834,7 +883,8 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     for (int k = 0; k < h->RA; ++k) { tau[k] = sym.tau[k]; wv[k] = sym.w[k]; mode[k] = sym.mode[k]; }
     for (int k = 0; k < h->RP; ++k) { tau[h->RA + k] = pc.tau[k]; wv[h->RA + k] = pc.w[k]; mode[h->RA + k] = -1; }
     do {
-        if (cudaMemcpy(h->lam, lam.data(), sizeof(double) * n, cudaMemcpyHostToDevice) ||
+        if ((varcoef && cudaMemcpy(h->V, Vh.data(), sizeof(double) * Vh.size(), cudaMemcpyHostToDevice)) ||
+            cudaMemcpy(h->lam, lam.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice) ||
             cudaMemcpy(h->sintab, tab.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice)) { rc = FC_ECUDA; break; }
         if (cudaMalloc(&dtau, sizeof(double) * RT) || cudaMalloc(&dw, sizeof(double) * RT) ||
             cudaMalloc(&dmode, sizeof(int) * RT)) { rc = FC_ECUDA; break; }
@@ -843,8 +893,8 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         cudaMemcpy(dmode, mode.data(), sizeof(int) * RT, cudaMemcpyHostToDevice);
         const long long bsE = (long long)n * h->RA;
         const long long bsP = (long long)n * h->RP;
-        launch_build_symbol(st, n, d, h->lam, dtau, dw, dmode, h->RA, h->EA, n, bsE, h->xiA);
-        launch_build_symbol(st, n, d, h->lam, dtau + h->RA, dw + h->RA, dmode + h->RA, h->RP, h->EP,
+        launch_build_symbol(st, n, d, h->lam, n, dtau, dw, dmode, h->RA, h->EA, n, bsE, h->xiA);
+        launch_build_symbol(st, n, d, h->lam, n, dtau + h->RA, dw + h->RA, dmode + h->RA, h->RP, h->EP,
                             n, bsP, h->xiP);
         // mode Grams GE_l = E_l diag(xi^2) E_l^T  (weighted side-matrix Grams of the symbols)
         const long long nn = (long long)n * n;
@@ -930,13 +980,18 @@ static int apply_common(fc_handle h, const fc_cp* x, fc_cp* y, void* stream, boo
     KRIn kr;
     int rc = kr_from(h, st, xc, precond ? 1 : 0, kr);
     if (rc) return rc;
-    // y_l = F (E_l[:,k] . Yh_l[:,j]) for all (k, j), weights xa_k xb_j
+    // y_l = F (E_l[:,k] . Yh_l[:,j]) for all (k, j), weights xa_k xb_j (F: the inverse
+    // transform of mode l, DST-I or the stiffness eigenbasis V_l)
     LdSine F{h->sintab, 2 * (h->n + 1)};
     const long long bsE = (long long)h->n * R;
-    for (int l = 0; l < h->d; ++l)
-        gemm_p(h->prec, st, h->n, (int)K, h->n, F,
-             LdKR{kr.E + l * bsE, h->n, 0, kr.Yh + (long long)l * h->n * h->KIN, h->n, 0, kr.S}, 1.0,
-             0.0, y->U[l], y->ld);
+    for (int l = 0; l < h->d; ++l) {
+        const LdKR kl{kr.E + l * bsE, h->n, 0, kr.Yh + (long long)l * h->n * h->KIN, h->n, 0, kr.S};
+        if (h->V)
+            gemm_p(h->prec, st, h->n, (int)K, h->n, LdN{h->V + (long long)l * h->n * h->n, h->n, 0},
+                   kl, 1.0, 0.0, y->U[l], y->ld);
+        else
+            gemm_p(h->prec, st, h->n, (int)K, h->n, F, kl, 1.0, 0.0, y->U[l], y->ld);
+    }
     launch_outer_weights(st, R, kr.xa, kr.S, kr.xb, y->xi);
     CKL();
     y->rank = (int)K;
@@ -1036,7 +1091,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         if (h->spectral && X.rank > 0) {
             const double* xin[3] = {X.U[0], X.U[1], X.U[2]};
             double* uo[3] = {u->U[0], u->U[1], u->U[2]};
-            dst_cols(h, st, X.rank, xin, X.ld, uo, u->ld);
+            dst_cols(h, st, X.rank, xin, X.ld, uo, u->ld, false);
         } else {
             for (int l = 0; l < h->d; ++l)
                 if (X.rank > 0)
@@ -1066,7 +1121,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
             const long long nK = (long long)h->n * h->KIN;
             const double* rin[3] = {R.U[0], R.U[1], R.U[2]};
             double* tmp[3] = {w.Yh, w.Yh + nK, w.Yh + 2 * nK};
-            dst_cols(h, st, R.rank, rin, R.ld, tmp, h->n);
+            dst_cols(h, st, R.rank, rin, R.ld, tmp, h->n, true);
             for (int l = 0; l < h->d; ++l)
                 CK(cudaMemcpy2DAsync(R.U[l], sizeof(double) * R.ld, tmp[l], sizeof(double) * h->n,
                                      sizeof(double) * h->n, R.rank, cudaMemcpyDeviceToDevice, st));
@@ -1180,24 +1235,43 @@ int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev
     const int n = h->n;
     LdSine F{h->sintab, 2 * (n + 1)};
     const long long nn = (long long)n * n;
-    // y = (F x .. x F) x  by d axis passes of a sine-matrix product
-    auto dst_all = [&](const double* in, double* out) -> int {
-        if (h->d == 2) {
-            gemm(st, n, n, n, F, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);            // axis 0
-            gemm(st, n, n, n, LdN{dev_tmp, n, 0}, F, 1.0, 0.0, out, n);           // axis 1
-        } else {
-            gemm(st, n, (int)nn, n, F, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);      // axis 0
-            gemm(st, n, n, n, LdN{dev_tmp, n, nn}, F, 1.0, 0.0, out, n, nn, n);   // axis 1 per i3
-            gemm(st, (int)nn, n, n, LdN{out, (int)nn, 0}, F, 1.0, 0.0, dev_tmp, (int)nn);  // axis 2
+    // y = (T_1 x .. x T_d) x  by d axis passes: T_l the DST-I (symmetric), or for per-mode
+    // eigenbases V_l^T (forward) and V_l (back)
+    auto dst_all = [&](const double* in, double* out, bool forward) -> int {
+        if (!h->V) {
+            if (h->d == 2) {
+                gemm(st, n, n, n, F, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);            // axis 0
+                gemm(st, n, n, n, LdN{dev_tmp, n, 0}, F, 1.0, 0.0, out, n);           // axis 1
+            } else {
+                gemm(st, n, (int)nn, n, F, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);      // axis 0
+                gemm(st, n, n, n, LdN{dev_tmp, n, nn}, F, 1.0, 0.0, out, n, nn, n);   // axis 1 per i3
+                gemm(st, (int)nn, n, n, LdN{out, (int)nn, 0}, F, 1.0, 0.0, dev_tmp, (int)nn);  // axis 2
+                CK(cudaMemcpyAsync(out, dev_tmp, sizeof(double) * nn * n, cudaMemcpyDeviceToDevice, st));
+            }
+            return FC_OK;
+        }
+        const double* V0 = h->V;
+        const double* V1 = h->V + nn;
+        const double* V2 = h->V + 2 * nn;
+        const long long cols0 = (h->d == 2) ? n : nn;
+        // axis 0: T_0 x ;  axes 1, 2: x T^T, i.e. x V (forward) or x V^T (back)
+        if (forward) gemm(st, n, (int)cols0, n, LdT{V0, n, 0}, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);
+        else gemm(st, n, (int)cols0, n, LdN{V0, n, 0}, LdN{in, n, 0}, 1.0, 0.0, dev_tmp, n);
+        const int b1 = (h->d == 2) ? 1 : n;
+        if (forward) gemm(st, n, n, n, LdN{dev_tmp, n, nn}, LdN{V1, n, 0}, 1.0, 0.0, out, n, nn, b1);
+        else gemm(st, n, n, n, LdN{dev_tmp, n, nn}, LdT{V1, n, 0}, 1.0, 0.0, out, n, nn, b1);
+        if (h->d == 3) {
+            if (forward) gemm(st, (int)nn, n, n, LdN{out, (int)nn, 0}, LdN{V2, n, 0}, 1.0, 0.0, dev_tmp, (int)nn);
+            else gemm(st, (int)nn, n, n, LdN{out, (int)nn, 0}, LdT{V2, n, 0}, 1.0, 0.0, dev_tmp, (int)nn);
             CK(cudaMemcpyAsync(out, dev_tmp, sizeof(double) * nn * n, cudaMemcpyDeviceToDevice, st));
         }
         return FC_OK;
     };
-    int rc = dst_all(dev_rhs, dev_u);
+    int rc = dst_all(dev_rhs, dev_u, true);
     if (rc) return rc;
-    launch_full_scale(st, h->d, n, h->lam, h->spec.a, h->spec.sn, h->spec.b, h->spec.sp,
+    launch_full_scale(st, h->d, n, h->lam, n, h->spec.a, h->spec.sn, h->spec.b, h->spec.sp,
                       h->spec.c, dev_u);
-    rc = dst_all(dev_u, dev_u);
+    rc = dst_all(dev_u, dev_u, false);
     if (rc) return rc;
     CKL();
     CK(cudaStreamSynchronize(st));

@@ -41,9 +41,9 @@ void launch_select_terms(cudaStream_t st, const double* mu, int ldmu, const int*
 // ---- k_tensor.cu ---------------------------------------------------------------------
 struct Piece { const double* xi; const double* U[3]; int ld; int K; double scale; };
 
-void launch_build_symbol(cudaStream_t st, int n, int d, const double* lam, const double* tau,
-                         const double* w, const int* mode, int R, double* E, int lde,
-                         long long bsE, double* xi);
+void launch_build_symbol(cudaStream_t st, int n, int d, const double* lam, int lstride,
+                         const double* tau, const double* w, const int* mode, int R, double* E,
+                         int lde, long long bsE, double* xi);
 // out columns = normalised columns of the pieces (in order); weights scale*xi*prod norms.
 void launch_concat_normalize(cudaStream_t st, int d, int n, Piece p0, Piece p1, double* U,
                              int ldo, long long bsU, double* w);
@@ -97,9 +97,10 @@ void launch_inner_reduce(cudaStream_t st, int d, int Rx, int Ry, const double* x
                          const double* eta, const double* M, int ldm, long long bsM, double* out);
 void launch_to_full(cudaStream_t st, int d, int n, int R, const double* xi, const double* U0,
                     const double* U1, const double* U2, int ld, double* dense);
-// u_hat[i] /= g(rho_i), g = ga rho^-sn + gb rho^sp + gc (full-format eigenbasis solve)
-void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double ga, double sn,
-                       double gb, double sp, double gc, double* x);
+// u_hat[i] /= g(rho_i), g = ga rho^-sn + gb rho^sp + gc, rho_i = sum_l lam[l*lstride + i_l]
+// (full-format eigenbasis solve)
+void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, int lstride, double ga,
+                       double sn, double gb, double sp, double gc, double* x);
 void launch_copy_weights(cudaStream_t st, int K, const double* src, double scale, double* dst);
 // w[(k,j)] = xa[k] * xb[j]
 void launch_outer_weights(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,

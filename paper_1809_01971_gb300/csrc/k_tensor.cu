@@ -23,9 +23,9 @@ __global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN,
 //   E_l[i, k] = exp(-tau_k lambda_i) * (l == mode_k ? lambda_i : 1),
 // normalised to unit columns; xi_k = w_k * prod_l ||E_l[:, k]||.  One CTA per term.
 // ---------------------------------------------------------------------------------------
-__global__ void build_symbol_kernel(int n, int d, const double* lam, const double* tau,
-                                    const double* w, const int* mode, double* E, int lde,
-                                    long long bsE, double* xi)
+__global__ void build_symbol_kernel(int n, int d, const double* lam, int lstride,
+                                    const double* tau, const double* w, const int* mode, double* E,
+                                    int lde, long long bsE, double* xi)
 {
     __shared__ double red[32];
     const int k = blockIdx.x;
@@ -35,9 +35,10 @@ __global__ void build_symbol_kernel(int n, int d, const double* lam, const doubl
     for (int l = 0; l < d; ++l) {
         double* col = E + l * bsE + (long long)k * lde;
         double s = 0.0;
+        const double* lm = lam + (long long)l * lstride;     // spectrum of mode l
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double v = exp(-t * lam[i]);
-            if (l == mk) v *= lam[i];
+            double v = exp(-t * lm[i]);
+            if (l == mk) v *= lm[i];
             col[i] = v;
             s += v * v;
         }
@@ -50,12 +51,12 @@ __global__ void build_symbol_kernel(int n, int d, const double* lam, const doubl
     if (threadIdx.x == 0) xi[k] = w[k] * prod;
 }
 
-void launch_build_symbol(cudaStream_t st, int n, int d, const double* lam, const double* tau,
-                         const double* w, const int* mode, int R, double* E, int lde,
-                         long long bsE, double* xi)
+void launch_build_symbol(cudaStream_t st, int n, int d, const double* lam, int lstride,
+                         const double* tau, const double* w, const int* mode, int R, double* E,
+                         int lde, long long bsE, double* xi)
 {
     if (R <= 0) return;
-    note_launch(); build_symbol_kernel<<<R, 256, 0, st>>>(n, d, lam, tau, w, mode, E, lde, bsE, xi);
+    note_launch(); build_symbol_kernel<<<R, 256, 0, st>>>(n, d, lam, lstride, tau, w, mode, E, lde, bsE, xi);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -475,8 +476,8 @@ void launch_to_full(cudaStream_t st, int d, int n, int R, const double* xi, cons
     note_launch(); to_full_kernel<<<blocks, 256, 0, st>>>(d, n, R, xi, U0, U1, U2, ld, dense);
 }
 
-__global__ void full_scale_kernel(int d, int n, const double* lam, double ga, double sn,
-                                  double gb, double sp, double gc, double* x)
+__global__ void full_scale_kernel(int d, int n, const double* lam, int lstride, double ga,
+                                  double sn, double gb, double sp, double gc, double* x)
 {
     const long long tot = (d == 3) ? (long long)n * n * n : (long long)n * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
@@ -485,7 +486,7 @@ __global__ void full_scale_kernel(int d, int n, const double* lam, double ga, do
         long long rest = e / n;
         int i1 = (int)(rest % n);
         int i2 = (int)(rest / n);
-        double rho = lam[i0] + lam[i1] + (d == 3 ? lam[i2] : 0.0);
+        double rho = lam[i0] + lam[lstride + i1] + (d == 3 ? lam[2 * lstride + i2] : 0.0);
         double g = gc;
         if (ga != 0.0) g += ga * pow(rho, -sn);
         if (gb != 0.0) g += gb * pow(rho, sp);
@@ -493,13 +494,13 @@ __global__ void full_scale_kernel(int d, int n, const double* lam, double ga, do
     }
 }
 
-void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, double ga, double sn,
-                       double gb, double sp, double gc, double* x)
+void launch_full_scale(cudaStream_t st, int d, int n, const double* lam, int lstride, double ga,
+                       double sn, double gb, double sp, double gc, double* x)
 {
     long long tot = (d == 3) ? (long long)n * n * n : (long long)n * n;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 152 * 64) blocks = 152 * 64;
-    note_launch(); full_scale_kernel<<<blocks, 256, 0, st>>>(d, n, lam, ga, sn, gb, sp, gc, x);
+    note_launch(); full_scale_kernel<<<blocks, 256, 0, st>>>(d, n, lam, lstride, ga, sn, gb, sp, gc, x);
 }
 
 __global__ void copy_weights_kernel(int K, const double* src, double scale, double* dst)

@@ -23,6 +23,108 @@ std::vector<double> spectrum(int n) {
     return lam;
 }
 
+// 1D stiffness matrix of -(a u')' (Remark on variable coefficients, A_l = -grad^T a_l grad):
+// with a_half[i] = a((i + 1/2) h), i = 0..n, row i of the symmetric tridiagonal matrix has
+// diagonal (a_half[i] + a_half[i+1]) / h^2 and off-diagonal -a_half[i+1] / h^2 (Dirichlet).
+void stiffness_1d(int n, const double* a_half, std::vector<double>& diag, std::vector<double>& off) {
+    const double N2 = (n + 1.0) * (n + 1.0);
+    diag.assign(n, 0.0);
+    off.assign(n > 0 ? n - 1 : 0, 0.0);
+    for (int i = 0; i < n; ++i) diag[i] = (a_half[i] + a_half[i + 1]) * N2;
+    for (int i = 0; i + 1 < n; ++i) off[i] = -a_half[i + 1] * N2;
+}
+
+// Symmetric tridiagonal eigen-decomposition T = V diag(lam) V^T by implicit QR steps with the
+// Wilkinson shift (the shift is the eigenvalue of the trailing 2 x 2 block closer to its last
+// diagonal entry).  A step chases the bulge of one Givens rotation down the unreduced block;
+// each rotation acts on the 4 x 4 window around it, held densely, and on two columns of V.
+// Off-diagonals below 4e-16 (|d_i| + |d_i+1|) are set to zero (deflation).  Eigenvalues
+// ascending, eigenvectors orthonormal columns of V (n x n, column-major).  O(n^3) with the
+// vectors: meant for the 1D problems, n up to a few thousand.
+bool tridiag_eig(int n, std::vector<double> d, std::vector<double> e, std::vector<double>& lam,
+                 std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i + (size_t)i * n] = 1.0;
+    lam = d;
+    if (n <= 1) return n == 1;
+    e.resize(n - 1);
+    int guard = 0;
+    for (int q = n - 1; q > 0;) {
+        // deflate from the bottom
+        while (q > 0 && std::fabs(e[q - 1]) <= 4e-16 * (std::fabs(d[q - 1]) + std::fabs(d[q]))) {
+            e[q - 1] = 0.0;
+            --q;
+        }
+        if (q == 0) break;
+        int p = q - 1;
+        while (p > 0 && std::fabs(e[p - 1]) > 4e-16 * (std::fabs(d[p - 1]) + std::fabs(d[p]))) --p;
+        if (++guard > 60 * n) return false;
+        // Wilkinson shift from the trailing 2 x 2 block of the unreduced block [p, q]
+        const double t = 0.5 * (d[q - 1] - d[q]);
+        const double b2 = e[q - 1] * e[q - 1];
+        const double den = t + (t >= 0.0 ? 1.0 : -1.0) * std::sqrt(t * t + b2);
+        const double mu = d[q] - (den != 0.0 ? b2 / den : 0.0);
+        double x = d[p] - mu, z = e[p];
+        double bulge = 0.0;                      // T[k+1][k-1] entry created by the previous rotation
+        for (int k = p; k < q; ++k) {
+            // rotation G in the plane (k, k+1) with G^T [x; z] = [r; 0]
+            const double r = std::hypot(x, z);
+            const double c = (r > 0.0) ? x / r : 1.0, s = (r > 0.0) ? z / r : 0.0;
+            // window rows/cols k-1 .. k+2 (local 0..3), entries of the symmetric matrix
+            double W[4][4] = {{0}};
+            const int base = k - 1;
+            for (int a = 0; a < 4; ++a) {
+                const int ia = base + a;
+                if (ia < p || ia > q) continue;
+                W[a][a] = d[ia];
+                if (a + 1 < 4 && ia + 1 <= q) W[a][a + 1] = W[a + 1][a] = e[ia];
+            }
+            if (k > p) W[0][2] = W[2][0] = bulge;   // T[k+1][k-1]
+            // W <- G^T W G on local indices 1, 2
+            for (int a = 0; a < 4; ++a) {            // rows
+                const double u = W[1][a], v = W[2][a];
+                W[1][a] = c * u + s * v;
+                W[2][a] = -s * u + c * v;
+            }
+            for (int a = 0; a < 4; ++a) {            // columns
+                const double u = W[a][1], v = W[a][2];
+                W[a][1] = c * u + s * v;
+                W[a][2] = -s * u + c * v;
+            }
+            // write back the tridiagonal part and the new bulge T[k+2][k]
+            for (int a = 0; a < 4; ++a) {
+                const int ia = base + a;
+                if (ia < p || ia > q) continue;
+                d[ia] = W[a][a];
+                if (a + 1 < 4 && ia + 1 <= q) e[ia] = W[a][a + 1];
+            }
+            if (k > p) e[k - 1] = W[0][1];           // T[k][k-1] (the old bulge is annihilated)
+            bulge = (k + 2 <= q) ? W[1][3] : 0.0;    // T[k+2][k] = W[3][1]
+            // V <- V G
+            double* vk = &V[(size_t)k * n];
+            double* vk1 = &V[(size_t)(k + 1) * n];
+            for (int i = 0; i < n; ++i) {
+                const double u = vk[i], v = vk1[i];
+                vk[i] = c * u + s * v;
+                vk1[i] = -s * u + c * v;
+            }
+            if (k + 1 < q) { x = e[k]; z = bulge; }
+        }
+    }
+    // ascending order
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] < d[b]; });
+    std::vector<double> Vs((size_t)n * n);
+    lam.resize(n);
+    for (int j = 0; j < n; ++j) {
+        lam[j] = d[idx[j]];
+        std::copy(&V[(size_t)idx[j] * n], &V[(size_t)idx[j] * n] + n, &Vs[(size_t)j * n]);
+    }
+    V.swap(Vs);
+    return true;
+}
+
 // Symmetric eigenvalues/vectors of a small dense matrix by cyclic Jacobi (row-major a, m x m).
 static void small_sym_eig(std::vector<double>& a, int m, std::vector<double>& w,
                           std::vector<double>& v) {
@@ -149,10 +251,8 @@ double SymbolSpec::eval(double rho) const {
     return g;
 }
 
-bool build_symbol_nodes(const std::vector<double>& lam, int d, const SymbolSpec& g, double delta,
+bool build_symbol_nodes(double rmin, double rmax, int d, const SymbolSpec& g, double delta,
                         SymbolNodes& out) {
-    const int n = (int)lam.size();
-    const double rmin = d * lam[0], rmax = d * lam[n - 1];
     const double B = rmax / rmin;
     out = SymbolNodes();
     out.rho_min = rmin;
@@ -220,12 +320,12 @@ bool build_symbol_nodes(const std::vector<double>& lam, int d, const SymbolSpec&
     return true;
 }
 
-bool build_inverse_power_nodes(const std::vector<double>& lam, int d, double s, double delta,
+bool build_inverse_power_nodes(double rmin, double rmax, int d, double s, double delta,
                                SymbolNodes& out) {
     SymbolSpec g;
     g.a = 1.0;
     g.sn = s;
-    return build_symbol_nodes(lam, d, g, delta, out);
+    return build_symbol_nodes(rmin, rmax, d, g, delta, out);
 }
 
 // Least squares min ||A x - b|| (A is m x k column-major, m >= k) by Householder QR.
@@ -261,13 +361,11 @@ static bool lstsq(std::vector<double> A, int m, int k, std::vector<double> b, st
     return true;
 }
 
-bool build_precond_nodes(const std::vector<double>& lam, int d, const SymbolSpec& gs, int rank,
+bool build_precond_nodes(double rmin, double rmax, const SymbolSpec& gs, int rank,
                          SymbolNodes& out) {
     // Fit p(rho) = sum_k w_k exp(-tau_k rho) to 1/g(rho) by least squares of p*g - 1 on a
     // geometric grid of [rho_min, rho_max], nodes tau_k geometric in
     // [0.2/rho_max, 20/rho_min]; columns scaled to unit norm before the solve.
-    const int n = (int)lam.size();
-    const double rmin = d * lam[0], rmax = d * lam[n - 1];
     out = SymbolNodes();
     out.rho_min = rmin;
     out.rho_max = rmax;

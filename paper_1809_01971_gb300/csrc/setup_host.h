@@ -43,15 +43,21 @@ ExpSum exp_sum(double s, double B, double delta, double s0);
 // The 1D spectrum lam (ascending) is passed in: lambda_k of the Laplacian, or lambda_k^alpha
 // for the directionally fractional operator (which then uses exponent 1).  Terms in the
 // order: the rho^-sn sum (r_minus terms), the Lemma 4.1 terms of rho^sp, the constant c.
-bool build_symbol_nodes(const std::vector<double>& lam, int d, const SymbolSpec& g, double delta,
+// [rmin, rmax] is the range of rho = sum_l lambda_{i_l, l} (sums of the per-mode extremes).
+bool build_symbol_nodes(double rmin, double rmax, int d, const SymbolSpec& g, double delta,
                         SymbolNodes& out);
 // Preconditioner: least-squares exponential sum of 1/g (rank terms) ...
-bool build_precond_nodes(const std::vector<double>& lam, int d, const SymbolSpec& g, int rank,
+bool build_precond_nodes(double rmin, double rmax, const SymbolSpec& g, int rank,
                          SymbolNodes& out);
 // ... or the sinc-quadrature exponential sum of rho^-s itself (the symbol g_1 = rho^-alpha of
 // Section 6, the exact inverse of A^alpha).
-bool build_inverse_power_nodes(const std::vector<double>& lam, int d, double s, double delta,
+bool build_inverse_power_nodes(double rmin, double rmax, int d, double s, double delta,
                                SymbolNodes& out);
+// Variable coefficients (Remark on generalised directionally fractional operators): the 1D
+// stiffness matrix of -(a u')' from a((i+1/2) h), i = 0..n, and its eigen-decomposition.
+void stiffness_1d(int n, const double* a_half, std::vector<double>& diag, std::vector<double>& off);
+bool tridiag_eig(int n, std::vector<double> d, std::vector<double> e, std::vector<double>& lam,
+                 std::vector<double>& V);
 
 // Compressed mode factor of a CP symbol: with X = E diag|xa| (n x R, E column-major with unit
 // columns), D the diagonal of its row norms and the thin SVD D^-1 X = U S V^T truncated to the

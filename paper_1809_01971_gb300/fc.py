@@ -19,6 +19,7 @@ import ctypes as C
 import os
 from typing import Optional
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,7 +45,8 @@ class fc_cp(C.Structure):
 class fc_setup_opts(C.Structure):
     _fields_ = [("delta_sym", C.c_double), ("precond_rank", C.c_int), ("max_rank", C.c_int),
                 ("max_tucker", C.c_int), ("max_input_rank", C.c_int), ("directional", C.c_int),
-                ("precision", C.c_int), ("op_kind", C.c_int), ("precond_kind", C.c_int)]
+                ("precision", C.c_int), ("op_kind", C.c_int), ("precond_kind", C.c_int),
+                ("coeff", C.c_void_p * 3)]
 
 
 class fc_setup_info(C.Structure):
@@ -220,13 +222,24 @@ class Handle:
 
 def fc_setup(n, d, alpha, beta, gamma, eps, delta_sym=0.0, precond_rank=0, max_rank=0,
              max_tucker=0, max_input_rank=0, directional=False, precision=0, op_kind=0,
-             precond_kind=0, device="cuda") -> Handle:
+             precond_kind=0, coeff=None, device="cuda") -> Handle:
     """precision: 0 FP64 contractions, 1 double-float FP32 contractions, 2 FP64-accurate
     digit products on the BF16 tensor cores for the large contractions.  op_kind: 0 the
     control operator, 1 A^alpha, 2 I + A^(2 alpha); precond_kind: 0 least-squares fit of 1/g,
-    1 the exponential sum of rho^-alpha (fc_setup_opts)."""
+    1 the exponential sum of rho^-alpha; coeff: per mode None or the n+1 values a_l((i+1/2)h)
+    of a variable coefficient (fc_setup_opts)."""
     o = fc_setup_opts(delta_sym, precond_rank, max_rank, max_tucker, max_input_rank,
                       1 if directional else 0, int(precision), int(op_kind), int(precond_kind))
+    keep = []                    # coefficient arrays stay alive through the call
+    if coeff is not None:
+        for l, a in enumerate(list(coeff)[:3]):
+            if a is None:
+                continue
+            arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+            if arr.shape != (int(n) + 1,):
+                raise ValueError(f"coeff[{l}] needs n+1 = {int(n) + 1} values a((i+1/2)h)")
+            keep.append(arr)
+            o.coeff[l] = arr.ctypes.data
     out = C.c_void_p()
     _check("fc_setup", lib().fc_setup(int(n), int(d), float(alpha), float(beta), float(gamma),
                                       float(eps), C.byref(o), C.byref(out)))

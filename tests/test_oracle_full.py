@@ -119,3 +119,35 @@ def test_test_operator_symbols_special_cases():
     A = full.dense_laplacian(b.shape)
     assert np.allclose(full.solve_full_op(b, 1, 1.0).reshape(-1), np.linalg.solve(A, b.reshape(-1)),
                        rtol=1e-11, atol=1e-14)
+
+
+def _coef(n, kind):
+    x = (np.arange(n + 1) + 0.5) / (n + 1)
+    return {0: 1.0 + 0.5 * np.sin(2 * np.pi * x), 1: np.exp(x), 2: 0.3 + x**2}[kind]
+
+
+def test_stiffness_with_unit_coefficient_is_the_laplacian():
+    for n in (1, 4, 9):
+        assert np.allclose(full.stiffness_1d(n, np.ones(n + 1)), full.laplacian_1d(n), rtol=1e-15)
+
+
+@pytest.mark.parametrize("ns,kinds", [((9, 11), (0, 1)), ((5, 6, 7), (0, None, 2)),
+                                      ((6, 5, 4), (1, 2, 0))])
+@pytest.mark.parametrize("op", [(0, 0.5, 1.0, 1e-2), (1, 0.3, 1.0, 1.0), (2, 0.5, 1.0, 1.0)])
+def test_varcoef_solve_matches_brute_force(ns, kinds, op):
+    """Separable variable coefficients: per-mode eigenbasis solve vs the dense operator from
+    the eigendecomposition of the assembled Kronecker sum."""
+    kind, alpha, beta, gamma_ = op
+    coeffs = [None if k is None else _coef(n, k) for n, k in zip(ns, kinds)]
+    rng = np.random.default_rng(400 + len(ns) + kind)
+    b = rng.standard_normal(ns)
+    u = full.solve_full_varcoef(b, coeffs, kind, alpha, beta, gamma_)
+    ref = full.brute_force_varcoef(b, coeffs, kind, alpha, beta, gamma_)
+    assert np.linalg.norm(u - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_varcoef_with_constant_coefficients_reduces_to_the_laplacian():
+    rng = np.random.default_rng(402)
+    b = rng.standard_normal((8, 9, 7))
+    u = full.solve_full_varcoef(b, [np.ones(9), None, np.ones(8)], 0, 0.5, 1.0, 1e-2)
+    assert np.linalg.norm(u - full.solve_full(b, 0.5, 1.0, 1e-2)) <= 1e-12 * np.linalg.norm(u)
