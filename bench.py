@@ -416,6 +416,7 @@ def main():
                            "l2": "flushed between steps (512 MiB write, untimed)",
                            "setup": "per operator, before timing",
                            "concurrency": "fc_solve_batched: one stream per problem, up to 16 host threads",
+                           "work_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"),
                            "pcg_iters": R["iters"]},
                 "forms": forms,
                 "vs_plain_fp64": value / results[0]["value"],

@@ -165,7 +165,10 @@ void launch_kr_cols(cudaStream_t st, int d, int n, int Ra, int S, const double* 
 }
 
 // ---------------------------------------------------------------------------------------
-// Counter-based Gaussian numbers for the sketches (splitmix64 + Box-Muller).
+// Counter-based Gaussian numbers for the sketches (splitmix64 + Box-Muller).  The transform
+// runs in FP32: a sketch needs Gaussian samples, not FP64-exact ones, and the FP64 log, square
+// root and cosine were a third of the sketch contraction's time (the generator runs in the
+// operand loader, once per tile that reads the element).  24-bit uniforms, |g| <= 5.8.
 // ---------------------------------------------------------------------------------------
 FC_DEV unsigned long long mix64(unsigned long long z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -176,9 +179,9 @@ FC_DEV unsigned long long mix64(unsigned long long z) {
 FC_DEV double gauss_at(unsigned long long seed, int a, int b) {
     unsigned long long h = mix64(seed ^ mix64(((unsigned long long)(unsigned)a << 32) | (unsigned)b));
     unsigned long long h2 = mix64(h);
-    double u1 = ((h >> 11) + 1) * (1.0 / 9007199254740993.0);   // (0, 1]
-    double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);         // [0, 1)
-    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    const float u1 = (float)((h >> 40) + 1) * (1.0f / 16777216.0f);   // (0, 1]
+    const float u2 = (float)(h2 >> 40) * (1.0f / 16777216.0f);         // [0, 1)
+    return (double)(sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2));
 }
 
 // B operand: Omega[k, t] * |w_k| with Omega Gaussian; batch item (mode) folds into the seed
