@@ -209,7 +209,10 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* opts,
  * A single solve keeps only a few of the 152 SMs busy (its small eigen-solves run on one CTA
  * each), so independent problems overlap on the device.  Handles and streams must be pairwise distinct (FC_EINVAL otherwise);
  * the calling thread's current device is used.  Returns FC_OK if every solve returned FC_OK,
- * else the first failing problem's code; info[i].status holds each problem's own status. */
+ * else the first failing problem's code; info[i].status holds each problem's own status.
+ * The streams overlap only if they have hardware work queues of their own.  CUDA gives 8
+ * unless CUDA_DEVICE_MAX_CONNECTIONS is set (up to 32) before the context is created;
+ * streams that share a queue serialise. */
 int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
                      const fc_solve_opts* opts, fc_solve_info* info, void* const* streams);
 
