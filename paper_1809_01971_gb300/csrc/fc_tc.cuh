@@ -23,8 +23,8 @@
 // LBO = 128 B between K-adjacent, SBO = 512 B between M/N-adjacent core matrices); the
 // operands are fused expressions (Khatri-Rao rows, scaled columns), so there is no
 // materialised tile for TMA to fetch.  Two stages of kTcKS = 32 along K are double-buffered:
-// one elected thread issues the MMAs of a stage and commits them to that stage's mbarrier
-// while all threads produce the next stage.  Every wait is bounded; on expiry the kernel
+// a dedicated warp issues the MMAs of a stage and commits them to that stage's mbarrier
+// while the 512 producer threads form the next stage.  Every wait is bounded; on expiry the kernel
 // records an error flag, frees its TMEM and returns.
 #pragma once
 // Included from fc_common.cuh after the loaders and the split-K pre-scale kernel.
@@ -37,7 +37,8 @@ constexpr int kTcDigits = 8;       // S
 constexpr int kTcBM = 128;         // MMA M (TMEM lane = output row)
 constexpr int kTcKS = 32;          // K per pipeline stage (two K = 16 MMA steps)
 constexpr int kTcKC = 448;         // K per CTA: 8 pairs * 448 * 64^2 < 2^24 (exact FP32 sums)
-constexpr int kTcThreads = 512;
+constexpr int kTcThreads = 512;     // digit producers (4 per row of the 128-row A tile)
+constexpr int kTcBlock = kTcThreads + 32;   // + one warp that issues the MMAs
 constexpr int kTcBadExp = 0x40000000;   // scale marker of a row / column holding Inf or NaN
 
 // Error flag of the tensor-core GEMMs of this translation unit (bounded wait expired).
@@ -327,15 +328,31 @@ FC_DEV void tc_store8(unsigned char* base, const unsigned long long (&F0)[8], co
 #undef FC_TC_PLANE
 }
 
+// Digits of 4 consecutive K values of one operand row: the low or high 8 bytes of a 16-byte
+// core-matrix row in each of the S planes.
+template <int PLANE>
+FC_DEV void tc_store4(unsigned char* base, const unsigned long long (&F0)[4], const uint32_t (&sg)[4]) {
+    unsigned long long F[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) F[q] = F0[q] + kTcOffset;
+#define FC_TC_PLANE4(s_)                                                                      \
+    *(uint2*)(base + (s_) * PLANE) =                                                          \
+        make_uint2(__byte_perm(tc_digit_f32<s_>(F[0], sg[0]), tc_digit_f32<s_>(F[1], sg[1]), 0x7632), \
+                   __byte_perm(tc_digit_f32<s_>(F[2], sg[2]), tc_digit_f32<s_>(F[3], sg[3]), 0x7632));
+    FC_TC_PLANE4(0) FC_TC_PLANE4(1) FC_TC_PLANE4(2) FC_TC_PLANE4(3)
+    FC_TC_PLANE4(4) FC_TC_PLANE4(5) FC_TC_PLANE4(6) FC_TC_PLANE4(7)
+#undef FC_TC_PLANE4
+}
+
 template <int BN, class LA, class LB>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcBlock, 1)
 gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
                LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
                int batch, int splits, int kchunk, unsigned long long* work)
 {
     using Sh = TcShape<BN>;
     constexpr int S = kTcDigits;
-    constexpr int NW = kTcThreads / 32;
+    constexpr int NW = kTcThreads / 32;              // producer warps; warp NW issues the MMAs
     constexpr int AQ = kTcThreads / kTcBM;           // threads per row of op(A)
     static_assert(S == 8, "digit planes are unrolled for S = 8");
     static_assert(AQ * 8 == kTcKS, "one 8-wide K group of op(A) per thread and stage");
@@ -346,7 +363,6 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
     __shared__ __align__(8) unsigned long long s_bar[2];
     __shared__ int s_ea[AQ][kTcBM];
     __shared__ int s_eb[BN];
-    __shared__ int s_bad;
 
     if (dM) M = min(M, *dM);
     if (dN) N = min(N, *dN);
@@ -370,13 +386,13 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
 
     // ---- scales: row exponents of op(A) (AQ threads per row), column exponents of op(B) --
     const TcTrans<LB> Bt{B};
-    {
+    if (tid < kTcThreads) {
         const int gi = m0 + row;
         const int kq = (kend - kbeg + AQ - 1) / AQ;
         const int ka = min(kend, kbeg + part * kq), kb = min(kend, ka + kq);
         s_ea[part][row] = (gi < M) ? tc_emax_row(A, gi, ka, kb, zb) : -(1 << 30);
     }
-    for (int j = warp; j < BN; j += NW) {
+    for (int j = warp; j < BN && warp < NW; j += NW) {
         const int gj = n0 + j;
         int fm = -(1 << 30);
         if (gj < N)
@@ -396,7 +412,6 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_saddr(&s_bar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_saddr(&s_bar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_bad = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -411,46 +426,63 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
                          | (1u << 7) | (1u << 10)           // A, B: BF16 (K-major)
                          | ((uint32_t)(BN >> 3) << 17)      // N / 8
                          | ((uint32_t)(kTcBM >> 4) << 24);  // M / 16
+    // Pipeline: producers fill stage st of buffer st & 1 once the MMAs of stage st - 2 (which
+    // read that buffer) have completed: one lane per warp waits on the buffer's mbarrier.  The
+    // MMA warp issues stage st after the block barrier and commits it to the same mbarrier, so
+    // the issue overlaps the production of stage st + 1.  The commit of stage t is the
+    // (t >> 1)-th completion of barrier t & 1: its phase parity is (t >> 1) & 1.  A failed
+    // wait ends the loop in every thread at the next barrier (__syncthreads_or).
     const int nst = (kend - kbeg + kTcKS - 1) / kTcKS;
-    uint32_t par0 = 0u, par1 = 0u;
+    const bool producer = tid < kTcThreads;
+    int issued = 0;                                   // stages issued (MMA thread)
+    bool bad = false;
     for (int st = 0; st < nst; ++st) {
         const int buf = st & 1;
         unsigned char* sa = smem + buf * Sh::STAGE;
         unsigned char* sb = sa + S * Sh::PA;
-        if (st >= 2) {            // the MMAs of stage st - 2 read this buffer
-            if (tid == 0 && !tc_wait(tc_saddr(&s_bar[buf]), buf ? par1 : par0)) s_bad = 1;
-            if (buf) par1 ^= 1u; else par0 ^= 1u;
-            __syncthreads();
-            if (s_bad) break;
-        }
-        const int k0 = kbeg + st * kTcKS;
-        // op(A) digits: thread <-> (row, 8-wide K group = one 16-byte core-matrix row)
-        {
-            const int gi = m0 + row;
-            unsigned long long F[8];
-            uint32_t sg[8];
-            if (gi < M) tc_fixed_row8(A, gi, k0 + part * 8, kend, zb, Ea, F, sg);
-            else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) { F[q] = 0ull; sg[q] = 0u; }
+        if (producer) {
+            if (st >= 2) {
+                int ok = 1;
+                if (lane == 0)
+                    ok = tc_wait(tc_saddr(&s_bar[buf]), (uint32_t)(((st - 2) >> 1) & 1)) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp();                         // the warp's writes follow the wait
+                bad = (ok == 0);
             }
-            tc_store8<Sh::PA>(sa + (row & 7) * 16 + (row >> 3) * 512 + part * 128, F, sg);
-        }
-        // op(B) digits: thread <-> (column j, 8-wide K group), 16-byte stores
-        for (int task = tid; task < BN * (kTcKS / 8); task += kTcThreads) {
-            const int j = task % BN, g = task / BN, gj = n0 + j;
-            unsigned long long F[8];
-            uint32_t sg[8];
-            if (gj < N) tc_fixed_row8(Bt, gj, k0 + g * 8, kend, zb, s_eb[j], F, sg);
-            else {
+            if (!bad) {
+                const int k0 = kbeg + st * kTcKS;
+                // op(A) digits: thread <-> (row, 8-wide K group = one 16-byte core-matrix row)
+                {
+                    const int gi = m0 + row;
+                    unsigned long long F[8];
+                    uint32_t sg[8];
+                    if (gi < M) tc_fixed_row8(A, gi, k0 + part * 8, kend, zb, Ea, F, sg);
+                    else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) { F[q] = 0ull; sg[q] = 0u; }
+                        for (int q = 0; q < 8; ++q) { F[q] = 0ull; sg[q] = 0u; }
+                    }
+                    tc_store8<Sh::PA>(sa + (row & 7) * 16 + (row >> 3) * 512 + part * 128, F, sg);
+                }
+                // op(B) digits: thread <-> (column j, 4-wide K group), 8-byte stores; the
+                // half-width groups spread B over twice as many warps
+                for (int task = tid; task < BN * (kTcKS / 4); task += kTcThreads) {
+                    const int j = task % BN, h = task / BN, gj = n0 + j;
+                    unsigned long long F[4];
+                    uint32_t sg[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        F[q] = 0ull; sg[q] = 0u;
+                        const int k = k0 + h * 4 + q;
+                        if (gj < N && k < kend) F[q] = tc_fixed_of(Bt, gj, k, zb, s_eb[j], sg[q]);
+                    }
+                    tc_store4<Sh::PB>(sb + (j & 7) * 16 + (j >> 3) * 512 + (h >> 1) * 128 + (h & 1) * 8,
+                                      F, sg);
+                }
             }
-            tc_store8<Sh::PB>(sb + (j & 7) * 16 + (j >> 3) * 512 + g * 128, F, sg);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        if (__syncthreads_or(bad ? 1 : 0)) { bad = true; break; }
+        if (tid == kTcThreads) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = tc_saddr(sa), b0 = tc_saddr(sb);
 #pragma unroll 1
@@ -465,17 +497,20 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
                         tc_mma(tmem + (uint32_t)(L * Sh::LSTRIDE), da, db, idesc, acc);
                     }
             tc_commit(tc_saddr(&s_bar[buf]));
+            issued = st + 1;
         }
     }
     // ---- epilogue: wait for the last commit, combine the levels, add to C ----------------
-    __syncthreads();
-    if (tid == 0 && !s_bad) {
-        const int lb = (nst - 1) & 1;
-        if (!tc_wait(tc_saddr(&s_bar[lb]), lb ? par1 : par0)) s_bad = 1;
+    {
+        int fail = bad ? 1 : 0;
+        if (!bad && tid == kTcThreads)
+            fail = tc_wait(tc_saddr(&s_bar[(nst - 1) & 1]), (uint32_t)(((nst - 1) >> 1) & 1)) ? 0 : 1;
+        if (bad && tid == kTcThreads && issued > 0)   // drain what was issued before freeing TMEM
+            (void)tc_wait(tc_saddr(&s_bar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
+        bad = __syncthreads_or(fail) != 0;
     }
-    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!s_bad) {
+    if (!bad && producer) {
         // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows) and the 8-column chunks
         // w / 4, w / 4 + NW / 4, ... of the tile
         const int q4 = warp & 3;
@@ -516,7 +551,7 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
         if (work && tid == 0)
             atomicAdd(work, (unsigned long long)(S * (S + 1) / 2) * 2ull * kTcBM * BN *
                                 (unsigned long long)(nst * kTcKS));
-    } else if (tid == 0) {
+    } else if (bad && tid == 0) {
         atomicExch(&g_tc_error, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -584,19 +619,19 @@ inline bool gemm_tc(cudaStream_t st, int M, int N, int K, LA A, LB B, double alp
     note_launch();
     switch (BN) {
         case 16:
-            gemm_tc_kernel<16, LA, LB><<<grid, kTcThreads, TcShape<16>::SMEM, st>>>(
+            gemm_tc_kernel<16, LA, LB><<<grid, kTcBlock, TcShape<16>::SMEM, st>>>(
                 M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
         case 32:
-            gemm_tc_kernel<32, LA, LB><<<grid, kTcThreads, TcShape<32>::SMEM, st>>>(
+            gemm_tc_kernel<32, LA, LB><<<grid, kTcBlock, TcShape<32>::SMEM, st>>>(
                 M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
         case 48:
-            gemm_tc_kernel<48, LA, LB><<<grid, kTcThreads, TcShape<48>::SMEM, st>>>(
+            gemm_tc_kernel<48, LA, LB><<<grid, kTcBlock, TcShape<48>::SMEM, st>>>(
                 M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
         default:
-            gemm_tc_kernel<64, LA, LB><<<grid, kTcThreads, TcShape<64>::SMEM, st>>>(
+            gemm_tc_kernel<64, LA, LB><<<grid, kTcBlock, TcShape<64>::SMEM, st>>>(
                 M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
             break;
     }
