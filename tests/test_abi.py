@@ -47,3 +47,22 @@ def test_setup_rejects_bad_parameters_without_touching_the_gpu():
                  (0, 2, 0.5, 1.0, 1e-2, 1e-8), (63, 2, 0.5, -1.0, 1e-2, 1e-8),
                  (63, 3, 0.5, 1.0, 0.0, 1e-8), (63, 3, 0.5, 1.0, 1e-2, 0.0)]:
         assert L.fc_setup(*args, None, ctypes.byref(out)) == fc.FC_EINVAL
+
+
+def test_import_sets_work_queues_unless_the_caller_did():
+    """Importing the package asks CUDA for 32 hardware work queues, so that the streams of a
+    batched solve do not serialise behind each other, and keeps a value the caller set."""
+    import subprocess
+    import sys
+    code = ("import os, sys; sys.path.insert(0, {root!r}); import paper_1809_01971_gb300; "
+            "print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'])").format(root=ROOT)
+    env = {k: v for k, v in os.environ.items() if k != "CUDA_DEVICE_MAX_CONNECTIONS"}
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "32"
+    env["CUDA_DEVICE_MAX_CONNECTIONS"] = "4"
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "4"
