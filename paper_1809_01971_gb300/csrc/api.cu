@@ -301,8 +301,10 @@ bool check_cp(const fc_ctx* h, const fc_cp* x, bool output) {
     return true;
 }
 
-// DST-I of `cols` columns of every mode: out_l = F in_l (Section 3.2, F = F^T = F^{-1})
-void dst_cols(fc_ctx* h, cudaStream_t st, int cols, const double* const in[3], int ldi,
+// Mode-wise transform to the operator's eigenbasis and back, on `cols` columns of every mode:
+// the DST-I out_l = F in_l for the Laplacian (Section 3.2, F = F^T = F^{-1}); with per-mode
+// eigenbases V_l (variable coefficients), out_l = V_l^T in_l forward and V_l in_l back.
+void eig_transform_cols(fc_ctx* h, cudaStream_t st, int cols, const double* const in[3], int ldi,
               double* const out[3], int ldo, bool forward) {
     if (cols <= 0) return;
     const int n = h->n;
@@ -535,7 +537,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     if (kr && !h->spectral) {
         const double* in[3] = {w.Z, w.Z + nC, w.Z + 2 * nC};
         double* o[3] = {w.Zr, w.Zr + nC, w.Zr + 2 * nC};
-        dst_cols(h, st, rz, in, n, o, n, false);
+        eig_transform_cols(h, st, rz, in, n, o, n, false);
         Zuse = w.Zr;
     }
     for (int l = 0; l < d; ++l)
@@ -568,7 +570,7 @@ int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, int which, KRIn& kr) {
                 CK(cudaMemcpy2DAsync(o[l], sizeof(double) * h->n, in[l], sizeof(double) * x.ld,
                                      sizeof(double) * h->n, x.rank, cudaMemcpyDeviceToDevice, st));
     } else {
-        dst_cols(h, st, x.rank, in, x.ld, o, h->n, true);
+        eig_transform_cols(h, st, x.rank, in, x.ld, o, h->n, true);
     }
     if (which == 1) {
         kr.xa = h->xiP; kr.E = h->EP; kr.Ra = h->RP; kr.bsE = (long long)h->n * h->RP; kr.GE = h->GEP;
@@ -1091,7 +1093,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         if (h->spectral && X.rank > 0) {
             const double* xin[3] = {X.U[0], X.U[1], X.U[2]};
             double* uo[3] = {u->U[0], u->U[1], u->U[2]};
-            dst_cols(h, st, X.rank, xin, X.ld, uo, u->ld, false);
+            eig_transform_cols(h, st, X.rank, xin, X.ld, uo, u->ld, false);
         } else {
             for (int l = 0; l < h->d; ++l)
                 if (X.rank > 0)
@@ -1121,7 +1123,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
             const long long nK = (long long)h->n * h->KIN;
             const double* rin[3] = {R.U[0], R.U[1], R.U[2]};
             double* tmp[3] = {w.Yh, w.Yh + nK, w.Yh + 2 * nK};
-            dst_cols(h, st, R.rank, rin, R.ld, tmp, h->n, true);
+            eig_transform_cols(h, st, R.rank, rin, R.ld, tmp, h->n, true);
             for (int l = 0; l < h->d; ++l)
                 CK(cudaMemcpy2DAsync(R.U[l], sizeof(double) * R.ld, tmp[l], sizeof(double) * h->n,
                                      sizeof(double) * h->n, R.rank, cudaMemcpyDeviceToDevice, st));

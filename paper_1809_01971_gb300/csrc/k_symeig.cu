@@ -442,6 +442,18 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         else if (e_ < nwork) { const int e2 = e_ - nblk; itA[t] = -1 - e2 % m; itB[t] = e2 / m; nit = t + 1; }
     }
     for (int sweep = 0; sweep < 15; ++sweep) {
+        // A sweep rotates some pair only if some off-diagonal entry passes the rotation test
+        // now (a round without rotations leaves the matrix as it is), so one pass over all
+        // entries with the same test ends the iteration without a sweep of empty rounds.
+        int hot = 0;
+        for (int e_ = tid; e_ < m * m; e_ += blockDim.x) {
+            const int p = e_ % m, q = e_ / m;
+            if (p < q) {
+                const float app = a[p * S + p], aqq = a[q * S + q], apq = a[p * S + q];
+                if (fabsf(apq) > fmaxf(1e-6f * sqrtf(fabsf(app * aqq)), floorRel)) hot = 1;
+            }
+        }
+        if (!__syncthreads_or(hot)) break;
         if (tid == 0) anyRot = 0;
         __syncthreads();
         for (int rnd = 0; rnd < m - 1; ++rnd) {
