@@ -4,7 +4,7 @@ fun     = X -> F(A) X with the control symbol (eqn:forControl times beta),
 precond = X -> P(A) X with the fitted inverse symbol,
 trunc   = RHOSVD truncation (oracle.truncate).
 
-Readings (listed in DESIGN.md): B is column-normalised on entry (same tensor);
+Readings: B is column-normalised on entry (same tensor);
 mat-vec outputs are truncated in their Khatri-Rao representation
 (truncate(normalize=False)); X^(0) = 0 so R^(0) = B; "R sufficiently
 small" is the recursive ||R^(k+1)|| / ||B|| <= tol; k_max = 100 (the paper's

@@ -13,7 +13,7 @@ exp(-t rho) = prod_l exp(-t lambda_{i_l}), so a quadrature sum
 sum_k c_k exp(-t_k rho) is a CP tensor of rank = number of nodes
 (eqn:Func_of_rho).
 
-Readings where the paper is silent or garbled (listed in the design doc):
+Readings where the paper is silent or garbled:
   * Substitution.  The paper substitutes t = log(1+e^u); its right tail then
     decays only like exp(-rho u) and needs about twice the nodes.  We use
     t = e^u (same trapezoidal sinc rule, eqn:Sinc_quadr_trunc, applied to

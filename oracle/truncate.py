@@ -16,7 +16,7 @@ Steps (the paper's order):
      each r_1 x r_2 slice; rank <= r_3 min(r_1, r_2) <= r^2.
   4. Side matrices of the result U'_l = Z_l C'_l (eqn:two_level).
 
-Readings (the paper does not state the thresholds; listed in the design doc):
+Readings (the paper does not state the thresholds):
   * Side-matrix weighting: W_l = U_l diag(|xi|) with U_l column-normalised and
     xi carrying the term norms, so the singular values are in the units of T.
   * Stage-1 rank: smallest r_l with (sum_{k>r_l} sigma_{l,k}^2)^(1/2)
