@@ -66,3 +66,26 @@ def test_import_sets_work_queues_unless_the_caller_did():
                          timeout=300)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "4"
+
+
+def test_header_is_plain_c_and_links_from_c(tmp_path):
+    """include/fc.h compiles as pedantic C99 and a C program links against libfc.so and gets
+    the host-only answers (argument errors, status strings) without a GPU."""
+    import shutil
+    import subprocess
+    from paper_1809_01971_gb300 import fc
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        import pytest
+        pytest.skip("gcc not available")
+    fc.lib()                                     # built in-tree
+    libdir = os.path.dirname(fc.LIB_PATH)
+    exe = str(tmp_path / "abi_from_c")
+    subprocess.run([gcc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror",
+                    "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_from_c.c"), "-o", exe,
+                    "-L", libdir, "-lfc", "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True, timeout=300)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.strip() == "ok"
