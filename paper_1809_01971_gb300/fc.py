@@ -220,6 +220,44 @@ class Handle:
             pass
 
 
+def fc_get_info(h: Handle) -> fc_setup_info:
+    """Sizes and ranks of a set-up (fc_get_info)."""
+    info = fc_setup_info()
+    _check("fc_get_info", lib().fc_get_info(h.ptr, C.byref(info)))
+    return info
+
+
+def fc_workspace_size(h: Handle) -> int:
+    """Bytes of device scratch the handle needs (fc_workspace_size)."""
+    nbytes = C.c_size_t()
+    _check("fc_workspace_size", lib().fc_workspace_size(h.ptr, C.byref(nbytes)))
+    return nbytes.value
+
+
+def fc_set_workspace(h: Handle, buf: torch.Tensor) -> None:
+    """Bind caller-owned device scratch (fc_set_workspace): a CUDA tensor of at least
+    fc_workspace_size(h) bytes whose data pointer is 256-byte aligned.  The handle keeps a
+    reference to it in place of the workspace fc_setup allocated."""
+    nbytes = buf.numel() * buf.element_size()
+    _check("fc_set_workspace", lib().fc_set_workspace(h.ptr, C.c_void_p(buf.data_ptr()), nbytes))
+    h.workspace = buf
+
+
+def fc_destroy(h: Handle) -> None:
+    """Release the handle's set-up tables (fc_destroy); the handle is unusable afterwards."""
+    h.destroy()
+
+
+def fc_strerror(code: int) -> str:
+    """Text of a status code (fc_strerror)."""
+    return lib().fc_strerror(int(code)).decode()
+
+
+def fc_last_cuda_error() -> str:
+    """Text of the last CUDA error the library recorded (fc_last_cuda_error)."""
+    return lib().fc_last_cuda_error().decode()
+
+
 def fc_setup(n, d, alpha, beta, gamma, eps, delta_sym=0.0, precond_rank=0, max_rank=0,
              max_tucker=0, max_input_rank=0, directional=False, precision=0, op_kind=0,
              precond_kind=0, coeff=None, device="cuda") -> Handle:

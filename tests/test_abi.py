@@ -89,3 +89,15 @@ def test_header_is_plain_c_and_links_from_c(tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stdout + out.stderr
     assert out.stdout.strip() == "ok"
+
+
+def test_binding_has_every_entry_point_by_name():
+    """The Python binding exposes each C entry point under the same name; the host-only ones
+    answer without a GPU."""
+    import paper_1809_01971_gb300 as pkg
+    from paper_1809_01971_gb300 import fc
+    missing = [n for n in sorted(_declared()) if not hasattr(pkg, n)]
+    assert not missing, missing
+    assert pkg.fc_strerror(fc.FC_ERANK) == "rank capacity exceeded"
+    assert pkg.fc_strerror(fc.FC_ETIMEOUT).startswith("a bounded wait")
+    assert isinstance(pkg.fc_last_cuda_error(), str)
