@@ -13,21 +13,28 @@ exp(-t rho) = prod_l exp(-t lambda_{i_l}), so a quadrature sum
 sum_k c_k exp(-t_k rho) is a CP tensor of rank = number of nodes
 (eqn:Func_of_rho).
 
-Readings where the paper is silent or garbled:
-  * Substitution.  The paper substitutes t = log(1+e^u); its right tail then
-    decays only like exp(-rho u) and needs about twice the nodes.  We use
-    t = e^u (same trapezoidal sinc rule, eqn:Sinc_quadr_trunc, applied to
-    rho^-s = Gamma(s)^-1 int_R exp(s u - rho e^u) du), whose right tail decays
-    double-exponentially.
-  * Scaling.  rho is scaled to [1, B] by rho_s = rho_min (eqn:Laplace_transf_rhom1).
-  * Step and truncation.  h = pi^2 / (ln(1/delta) + 3) (the paper's
-    h = kappa pi / sqrt(M) leaves kappa, M open); the sum is truncated
-    asymmetrically: on the right at the first node whose largest relative
-    contribution over rho in [1, B] is below delta/20.
-  * Left tail.  Nodes with t_k B < s0 (their exponentials are almost linear on
-    [1, B]) form a positive discrete measure; it is replaced by its m-point
-    Gauss rule (moments up to degree 2m-1 preserved, error <= s0^(2m)/(2m)!
-    relative).  This replaces hundreds of nodes for small s by m.
+The rule is the paper's, kept plain (every node of the truncated trapezoidal
+sum is a term of the symbol; nothing is merged or compressed):
+  * Substitution t = phi(u) = log(1 + e^u) (Section 4.2), so that
+    rho^-s = Gamma(s)^-1 int_R phi(u)^(s-1) phi'(u) exp(-rho phi(u)) du,
+    phi'(u) = 1/(1 + e^-u).
+  * Scaling: rho is scaled to [1, B] by rho_min (eqn:Laplace_transf_rhom1).
+  * Trapezoidal sinc sum (eqn:Sinc_quadr_trunc) with nodes u_k = k h,
+    k = -M_- .. M_+, t_k = phi(u_k), c_k = h phi(u_k)^(s-1) phi'(u_k) / Gamma(s).
+
+Readings where the paper leaves the parameters open (it writes
+h = kappa pi / sqrt(M) with unspecified kappa, M and a symmetric range):
+  * Truncation.  The integral cut at u = U, transformed back to t, is an
+    incomplete gamma function: the part of rho^-s beyond t_hi = phi(U) is
+    rho^-s Q(s, rho t_hi) and the part below t_lo is rho^-s P(s, rho t_lo)
+    (P, Q the regularised lower / upper incomplete gamma).  Over rho in [1, B]
+    the first is largest at rho = 1 and the second at rho = B, so
+    Q(s, t_hi) = delta/4 and P(s, B t_lo) = delta/4 fix both ends exactly:
+    M_- and M_+ need not be equal.
+  * Step.  h starts at 1 and shrinks by a factor 0.9 until the rule's largest
+    relative error on 3001 geometric points of [1, B] is <= delta; the
+    trapezoidal error decays like exp(-pi^2 / h) (the integrand is analytic
+    in the strip |Im u| < pi/2), bound (ff6).
   * Positive power.  gamma rho^alpha = gamma rho * rho^(alpha-1) (Lemma 4.1):
     each node of the rho^(alpha-1) sum yields d rank-one terms whose mode-m
     factor is lambda * exp(-t lambda).  At alpha = 1 the term is exactly
@@ -45,87 +52,61 @@ import math
 from dataclasses import dataclass
 
 import numpy as np
-from scipy.special import gamma as Gamma
+from scipy.special import gammaincinv, gammainccinv, gammaln
 
 from .spectrum import eigenvalues
 
 
-def sinc_step(delta: float) -> float:
-    """Trapezoid step h for a target relative accuracy delta."""
-    return math.pi**2 / (math.log(1.0 / delta) + 3.0)
+def phi(u):
+    """t = phi(u) = log(1 + e^u) (the substitution of Section 4.2)."""
+    return np.logaddexp(0.0, u)
 
 
-def tail_points(delta: float, s0: float) -> int:
-    """Smallest m with s0^(2m)/(2m)! <= delta/100 (Gauss-rule remainder)."""
-    m = 1
-    while s0 ** (2 * m) / math.factorial(2 * m) > delta / 100.0:
-        m += 1
-    return m
+def phi_inverse(t: float) -> float:
+    """u with phi(u) = t: log(e^t - 1)."""
+    return math.log(math.expm1(t))
 
 
-def gauss_rule_discrete(t: np.ndarray, c: np.ndarray, m: int):
-    """m-point Gauss rule of the positive discrete measure sum_k c_k delta(t - t_k).
-
-    Discretised Stieltjes procedure: three-term recurrence of the monic
-    orthogonal polynomials evaluated at the support points, then the Jacobi
-    matrix eigen-decomposition (Golub-Welsch).  Returns (nodes, weights).
-    """
-    scale = t.max()
-    x = t / scale
-    mu0 = c.sum()
-    p_prev = np.zeros_like(x)
-    p = np.ones_like(x)
-    a = np.zeros(m)
-    b = np.zeros(m)
-    norm_prev = None
-    for j in range(m):
-        norm = np.sum(c * p * p)
-        a[j] = np.sum(c * x * p * p) / norm
-        if j > 0:
-            b[j] = norm / norm_prev
-        p_next = (x - a[j]) * p - (b[j] * p_prev if j > 0 else 0.0)
-        p_prev, p = p, p_next
-        norm_prev = norm
-    J = np.diag(a) + np.diag(np.sqrt(b[1:]), 1) + np.diag(np.sqrt(b[1:]), -1)
-    ev, V = np.linalg.eigh(J)
-    return ev * scale, mu0 * V[0, :] ** 2
+def tail_cuts(s: float, B: float, delta: float):
+    """(t_lo, t_hi): the parts of the Laplace integral below t_lo and above t_hi are at
+    most delta/4 of rho^-s for every rho in [1, B] (incomplete gamma functions)."""
+    t_hi = float(gammainccinv(s, delta / 4.0))
+    t_lo = float(gammaincinv(s, delta / 4.0)) / B
+    return t_lo, t_hi
 
 
-def exp_sum(s: float, B: float, delta: float = 1e-10, s0: float = 0.5):
-    """Nodes t_k and weights c_k with rho^-s ~ sum_k c_k exp(-t_k rho) on [1, B].
+def trapezoid_rule(s: float, B: float, delta: float, h: float):
+    """Nodes t_k and weights c_k of the truncated trapezoidal sum with step h
+    (eqn:Sinc_quadr_trunc with the substitution t = phi(u))."""
+    t_lo, t_hi = tail_cuts(s, B, delta)
+    k = np.arange(math.floor(phi_inverse(t_lo) / h), math.ceil(phi_inverse(t_hi) / h) + 1)
+    u = k * h
+    t = phi(u)
+    # c_k = h t_k^(s-1) phi'(u_k) / Gamma(s), formed in logarithms (t_k spans many decades)
+    logc = math.log(h) + (s - 1.0) * np.log(t) - np.logaddexp(0.0, -u) - gammaln(s)
+    return t, np.exp(logc)
 
-    Trapezoidal sinc quadrature (eqn:Sinc_quadr_trunc) of
-    Gamma(s)^-1 int_R exp(s u - rho e^u) du with nodes u_k = k h, t_k = e^(u_k),
-    c_k = h e^(s u_k) / Gamma(s); left tail merged by its Gauss rule.
-    """
+
+def rule_error(s: float, B: float, t: np.ndarray, c: np.ndarray, points: int = 3001) -> float:
+    """Largest relative error of sum_k c_k exp(-t_k rho) against rho^-s on a geometric grid
+    of [1, B]."""
+    rho = np.exp(np.linspace(0.0, math.log(B), points))
+    return float(np.max(np.abs((np.exp(-np.outer(rho, t)) @ c) * rho**s - 1.0)))
+
+
+def exp_sum(s: float, B: float, delta: float = 1e-10):
+    """Nodes t_k and weights c_k with rho^-s ~ sum_k c_k exp(-t_k rho) on [1, B] to relative
+    accuracy delta (the rule and its readings in the module docstring)."""
     if s <= 0.0:
         raise ValueError("s must be positive")
-    h = sinc_step(delta)
-    m = tail_points(delta, s0)
-    gs = Gamma(s)
-    k0 = int(math.floor(math.log(s0 / B) / h))
-    # left tail: k0 - L .. k0 - 1, L such that c_k / c_k0 < e^-46
-    L = int(math.ceil(46.0 / (s * h)))
-    kt = np.arange(k0 - L, k0, dtype=np.float64)
-    ut = kt * h
-    tt = np.exp(ut)
-    ct = h * np.exp(s * ut) / gs
-    tg, cg = gauss_rule_discrete(tt, ct, m)
-    # body: k0, k0+1, ... until the node is insignificant on [1, B]
-    tb, cb = [], []
-    k = k0
+    h = 1.0
     while True:
-        u = k * h
-        t = math.exp(u)
-        c = h * math.exp(s * u) / gs
-        r = min(max(1.0, s / t), B)
-        contrib = c * math.exp(-t * r) * r**s
-        if u > 0.0 and contrib < delta / 20.0:
-            break
-        tb.append(t)
-        cb.append(c)
-        k += 1
-    return np.concatenate([tg, tb]), np.concatenate([cg, cb])
+        t, c = trapezoid_rule(s, B, delta, h)
+        if rule_error(s, B, t, c) <= delta:
+            return t, c
+        h *= 0.9
+        if h < 1e-3:
+            raise RuntimeError("sinc rule did not reach the requested accuracy")
 
 
 def normalise_columns(xi, U):
