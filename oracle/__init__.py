@@ -29,6 +29,9 @@ Modules
               y = beta A^-alpha u (eqn:State), the directionally fractional
               Laplacian solve (Remark after Lemma 4.1), and dense
               eigendecomposition brute forces of both for small n.
+  eigerr      the error of a CP solution against the exact full-format solution
+              (eqn:DiagFLaplace3D), summed point by point over the whole eigen-index
+              grid in plain C (csrc/eigerr.c), no n^d array formed.
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, brute force or library routines; none is "parity unpinned".
