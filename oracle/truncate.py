@@ -80,7 +80,7 @@ def truncate(T, eps: float, max_rank: int, info: dict | None = None,
         return np.zeros(0), [np.zeros((n, 0)) for n in ns]
     wnorm = float(np.linalg.norm(xi))
     thr1 = eps * wnorm / math.sqrt(2.0 * d)
-    Z, C, e1 = [], [], 0.0
+    Z, C, e1, tails1 = [], [], 0.0, []
     for l in range(d):
         W = U[l] * np.abs(xi)[None, :]
         Zl, s, _ = np.linalg.svd(W, full_matrices=False)
@@ -89,6 +89,7 @@ def truncate(T, eps: float, max_rank: int, info: dict | None = None,
         r = next(i for i in range(len(tail)) if tail[i] <= thr1)
         r = max(1, min(r, max_tucker, len(s)))
         e1 += tail[r] ** 2
+        tails1.append(float(tail[r]))
         Z.append(Zl[:, :r])
         C.append(Zl[:, :r].T @ U[l])
     # Tucker core (eqn:coret)
@@ -128,5 +129,6 @@ def truncate(T, eps: float, max_rank: int, info: dict | None = None,
         out_U.append(Z[l] @ cols)
     if info is not None:
         info.update(ranks=[z.shape[1] for z in Z], rank=q,
-                    est_err=float(math.sqrt(e1 + e2**2)), core_norm=bnorm)
+                    est_err=float(math.sqrt(e1 + e2**2)), core_norm=bnorm, bases=Z,
+                    stage1_tails=tails1, stage2_err=float(e2), sigma=sig)
     return out_xi, out_U
