@@ -288,8 +288,8 @@ def main():
 
         def step(hs=hs, Us=Us, spectral=spectral):
             # the step's problems run concurrently, one stream each (fc_solve_batched)
-            return fc.fc_solve_batched(hs, Bs, Us, streams, tol=tols, eps=epss,
-                                       spectral=spectral)
+            return fc.fc_solve_batched(hs, Bs, Us, tol=tols, eps=epss, spectral=spectral,
+                                       stream=main_stream)
 
         for _ in range(args.warmup):
             step()
@@ -358,7 +358,8 @@ def main():
                 B.xi[:R_].copy_(xi_h, non_blocking=True)
                 B.U[:, :R_, :p.n].copy_(U_h, non_blocking=True)
             B.rank = R_
-        fc.fc_solve_batched(hsb, Bs, Usb, streams, tol=tols, eps=epss, spectral=FORMS[best][2])
+        fc.fc_solve_batched(hsb, Bs, Usb, tol=tols, eps=epss, spectral=FORMS[best][2],
+                            stream=main_stream)
         for (xo, Uo), p, U, s_ in zip(host_out, probs, Usb, streams):
             with torch.cuda.stream(s_):
                 xo.copy_(U.xi[:p.max_rank], non_blocking=True)

@@ -119,6 +119,9 @@ typedef struct fc_solve_opts {
                         /* and preconditioner are diagonal and inner products are unchanged    */
                         /* (F orthogonal), and X is transformed back once at exit; the same    */
                         /* result without the two DSTs per mat-vec [0]                          */
+    int precision;      /* contraction form of this solve: 0 the handle's (fc_setup_opts.      */
+                        /* precision); 1 FP64, 2 double-float FP32, 3 tensor-core digits, so   */
+                        /* one set-up serves every form [0]                                     */
 } fc_solve_opts;
 
 typedef struct fc_solve_info {
@@ -204,17 +207,20 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* opts,
              fc_solve_info* info, void* stream);
 
 /* `count` independent solves (each as fc_solve on its own handle, right-hand side rhs[i],
- * solution u[i], options opts[i] (opts may be NULL), info[i]), run concurrently: a pool of at
- * most 16 host threads takes the problems in order, each driving Algorithm 1 on streams[i].
- * A single solve keeps only a few of the 152 SMs busy (its small eigen-solves run on one CTA
- * each), so independent problems overlap on the device.  Handles and streams must be pairwise distinct (FC_EINVAL otherwise);
- * the calling thread's current device is used.  Returns FC_OK if every solve returned FC_OK,
- * else the first failing problem's code; info[i].status holds each problem's own status.
- * The streams overlap only if they have hardware work queues of their own.  CUDA gives 8
- * unless CUDA_DEVICE_MAX_CONNECTIONS is set (up to 32) before the context is created;
- * streams that share a queue serialise. */
+ * solution u[i], options opts[i] (opts may be NULL), info[i]), run concurrently.  A pool of at
+ * most 16 host threads takes the problems in order; each thread drives Algorithm 1 on a
+ * non-blocking worker stream of the library's own (16 per device, created on first use, kept
+ * until exit).  The worker streams start after the work already queued on `stream`, and
+ * `stream` waits for them before later work on it runs; the call returns when every solve has
+ * finished.  A single solve keeps only a few of the 152 SMs busy (its small eigen-solves run
+ * on one CTA each), so independent problems overlap on the device.  Handles must be pairwise
+ * distinct (FC_EINVAL otherwise: a handle's workspace serves one solve at a time); the calling
+ * thread's current device is used.  Returns FC_OK if every solve returned FC_OK, else the
+ * first failing problem's code; info[i].status holds each problem's own status.  The worker
+ * streams overlap only if they get hardware work queues of their own: CUDA gives 8 unless
+ * CUDA_DEVICE_MAX_CONNECTIONS is set (up to 32) before the context is created. */
 int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
-                     const fc_solve_opts* opts, fc_solve_info* info, void* const* streams);
+                     const fc_solve_opts* opts, fc_solve_info* info, void* stream);
 
 /* Expand a CP tensor to the full n^d array, column-major (i_1 fastest). */
 int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream);
@@ -245,6 +251,15 @@ int fc_inner_static(const fc_cp* x, const fc_cp* y, double* dev_out, void* strea
 void fc_destroy(fc_handle h);
 const char* fc_strerror(int code);
 const char* fc_last_cuda_error(void);
+
+/* Test hook; the paper has no counterpart.  Sets the iteration limit of the producer-side
+ * mbarrier waits of the tensor-core contraction kernel (default 2^24 polls, about 1 s) for the
+ * whole process and returns the previous limit in *previous (may be NULL).  With 0 those waits
+ * give up at once, so a test sees FC_ETIMEOUT from a tensor-core solve without faulting or
+ * hanging the GPU: the kernel stops producing, its MMA-issuing thread still drains the MMAs it
+ * issued with the full limit before the tensor memory is freed, and the call returns.
+ * iterations < 0: FC_EINVAL. */
+int fc_set_wait_limit(int iterations, int* previous);
 
 /* Number of CUDA kernels libfc has launched in this process so far (all handles, all
  * devices); a host-side counter for instrumentation, no synchronisation. */

@@ -25,6 +25,13 @@ namespace fc {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Tensor-core error flag of the calling thread's current handle call (a slot of that
+// handle's workspace; null outside handle calls) and the producer-side wait limit.
+static thread_local int* t_tc_flag = nullptr;
+static std::atomic<int> g_tc_wait_limit{kTcWaitFull};
+int* tc_error_target() { return t_tc_flag; }
+int tc_producer_wait_limit() { return g_tc_wait_limit.load(std::memory_order_relaxed); }
+
 // Instrumentation state: one enabled kernel class, a growing pool of event pairs.
 static std::mutex g_prof_mu;
 static std::atomic<int> g_prof_class{KC_NONE};
@@ -333,18 +340,37 @@ struct KRIn {           // implicit Khatri-Rao tensor sum_{k,j} xa_k xb_j (x)_l 
 };
 struct DenseIn { const double* w; const double* U; int ld; long long bs; int K; };
 
-// The tensor-core GEMMs record an expired bounded wait in a device flag (fc_tc.cuh; one
-// flag for the process); calls of a handle in that form read and clear it after their
-// final stream synchronisation.
-int tc_status(const fc_ctx* h) {
-    if (h->prec != GP_TC64) return FC_OK;
-    int flag = 0;
-    CK(cudaMemcpyFromSymbol(&flag, g_tc_error, sizeof(int)));
-    if (!flag) return FC_OK;
-    const int zero = 0;
-    CK(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)));
-    return FC_ETIMEOUT;
+// The tensor-core GEMMs of a handle call record an expired bounded wait in the flag slot
+// dims[D_FLAG] of the handle's workspace (HandleCall points the launches there and clears it
+// at entry).  The slot travels to the host with the truncation's dims copy (h->hint); calls
+// without a truncation copy it themselves (flag_to_host) before their synchronisation.
+int tc_status(const fc_ctx* h) { return h->hint[D_FLAG] ? FC_ETIMEOUT : FC_OK; }
+
+int flag_to_host(fc_ctx* h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h->hint + D_FLAG, h->w.dims + D_FLAG, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return FC_OK;
 }
+
+// Scope of one API call on a handle: the calling thread's tensor-core launches report into
+// the handle's flag slot, which starts cleared; the contraction form may be overridden.
+struct HandleCall {
+    fc_ctx* h;
+    int* prev_flag;
+    int prev_prec;
+    int rc = FC_OK;
+    HandleCall(fc_ctx* h_, cudaStream_t st, int prec_override = -1)
+        : h(h_), prev_flag(t_tc_flag), prev_prec(h_->prec) {
+        t_tc_flag = h->w.dims + D_FLAG;
+        h->hint[D_FLAG] = 0;
+        if (prec_override >= 0) h->prec = prec_override;
+        cudaError_t e = cudaMemsetAsync(h->w.dims + D_FLAG, 0, sizeof(int), st);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+    ~HandleCall() {
+        t_tc_flag = prev_flag;
+        h->prec = prev_prec;
+    }
+};
 
 // ---------------------------------------------------------------------------------------
 // Truncation (Section 5, RHOSVD canonical -> Tucker -> canonical).  Input either an
@@ -371,7 +397,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     const int cs = sketch ? CM - kHold : c;
     const unsigned long long seed = (h->seed += 0x9E3779B97F4A7C15ull);
     int* dims = w.dims;
-    CK(cudaMemsetAsync(dims, 0, sizeof(int) * D_SIZE, st));
+    CK(cudaMemsetAsync(dims, 0, sizeof(int) * D_FLAG, st));
     CK(cudaMemsetAsync(w.scal, 0, sizeof(double) * 64, st));
 
     // ---- stage 1: range of the weighted side matrices W_l = U_l diag|w| ------------------
@@ -739,6 +765,13 @@ int fc_prof_read(long long* launches, double* total_ms, double* work) {
     return FC_OK;
 }
 
+int fc_set_wait_limit(int iterations, int* previous) {
+    if (iterations < 0) return FC_EINVAL;
+    const int old = g_tc_wait_limit.exchange(iterations);
+    if (previous) *previous = old;
+    return FC_OK;
+}
+
 unsigned long long fc_launch_count(void) { return fc::g_launches.load(std::memory_order_relaxed); }
 
 int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
@@ -978,6 +1011,8 @@ static int apply_common(fc_handle h, const fc_cp* x, fc_cp* y, void* stream, boo
     const long long K = (long long)R * x->rank;
     if (K > y->cap) { y->rank = (int)std::min<long long>(K, 0x7fffffff); return FC_ERANK; }
     cudaStream_t st = (cudaStream_t)stream;
+    HandleCall call(h, st);
+    if (call.rc) return call.rc;
     CP xc = from_user(x);
     KRIn kr;
     int rc = kr_from(h, st, xc, precond ? 1 : 0, kr);
@@ -997,6 +1032,7 @@ static int apply_common(fc_handle h, const fc_cp* x, fc_cp* y, void* stream, boo
     launch_outer_weights(st, R, kr.xa, kr.S, kr.xb, y->xi);
     CKL();
     y->rank = (int)K;
+    if ((rc = flag_to_host(h, st))) return rc;
     CK(cudaStreamSynchronize(st));
     return tc_status(h);
 }
@@ -1015,6 +1051,8 @@ int fc_truncate(fc_handle h, const fc_cp* x, double eps, int max_rank, int norma
     if (!h->ws) return FC_EWORKSPACE;
     if (x->rank > h->w.cat.cap || x->rank > h->KMAX) { y->rank = x->rank; return FC_ERANK; }
     cudaStream_t st = (cudaStream_t)stream;
+    HandleCall call(h, st);
+    if (call.rc) return call.rc;
     CP xc = from_user(x), yc = from_user(y);
     int rc;
     if (normalize) {
@@ -1045,6 +1083,8 @@ int fc_apply_trunc(fc_handle h, int which, const fc_cp* x, double eps, int max_r
         return FC_EINVAL;
     if (!h->ws) return FC_EWORKSPACE;
     if (x->rank > h->KIN) { y->rank = x->rank; return FC_ERANK; }
+    HandleCall call(h, (cudaStream_t)stream);
+    if (call.rc) return call.rc;
     CP xc = from_user(x), yc = from_user(y);
     int rc = kr_trunc(h, (cudaStream_t)stream, xc, which, eps, max_rank, yc);
     y->rank = yc.rank;
@@ -1061,10 +1101,11 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
              fc_solve_info* info, void* stream) {
     if (!h || !check_cp(h, rhs, false) || !check_cp(h, u, true)) return FC_EINVAL;
     if (!h->ws) return FC_EWORKSPACE;
-    fc_solve_opts opts{1e-8, 0.0, 100, 0, 0};
+    fc_solve_opts opts{1e-8, 0.0, 100, 0, 0, 0};
     if (o) opts = *o;
     if (!(opts.tol > 0.0)) opts.tol = 1e-8;
     if (opts.kmax <= 0) opts.kmax = 100;
+    if (opts.precision < 0 || opts.precision > 3) return FC_EINVAL;
     const double eps = (opts.eps > 0.0) ? opts.eps : h->eps;
     const int cap = std::min(h->CAP, (opts.max_rank > 0) ? opts.max_rank : h->CAP);
     if (u->cap < cap) { u->rank = cap; return FC_ERANK; }
@@ -1075,6 +1116,10 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     h->stat_rmax = h->stat_bmax = 0;
     h->seed = fc_ctx::kSeed0;  // same sketches for every solve of a right-hand side: reproducible
     cudaStream_t st = (cudaStream_t)stream;
+    // contraction form of this solve: the handle's, or opts.precision - 1
+    HandleCall call(h, st, opts.precision > 0 ? (opts.precision == 3 ? GP_TC64 :
+                                                 opts.precision == 2 ? GP_DF32 : GP_F64) : -1);
+    if (call.rc) return call.rc;
     auto& w = h->w;
     CP B = from_user(rhs);
     CP &X = w.Xs, &R = w.Rs, &P = w.Ps, &Z = w.Zs, &S = w.Ss;
@@ -1102,7 +1147,10 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         }
         if (X.rank > 0) launch_copy_weights(st, X.rank, X.xi, bscale, u->xi);   // undo 1/||B||
         u->rank = X.rank;
+        if (int rf = flag_to_host(h, st)) return rf;
         CK(cudaStreamSynchronize(st));
+        if (status == FC_OK && tc_status(h)) status = FC_ETIMEOUT;
+        inf.status = status;
         if (info) *info = inf;
         return status;
     };
@@ -1184,38 +1232,81 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
 // few enough not to oversubscribe the host (16 cores on the GB300 machines).
 constexpr int kBatchWorkers = 16;
 
+namespace {
+// One non-blocking stream per batch worker and device, created on first use and kept for the
+// life of the process (a solve is a chain of small launches and host synchronisations on its
+// worker's stream).
+struct WorkerStreams {
+    std::mutex mu;
+    cudaStream_t s[64][kBatchWorkers] = {};
+    bool made[64] = {};
+};
+WorkerStreams g_workers;
+
+int worker_streams(int dev, cudaStream_t* out) {
+    if (dev < 0 || dev >= 64) return FC_EINVAL;
+    std::lock_guard<std::mutex> lock(g_workers.mu);
+    if (!g_workers.made[dev]) {
+        for (int i = 0; i < kBatchWorkers; ++i)
+            CK(cudaStreamCreateWithFlags(&g_workers.s[dev][i], cudaStreamNonBlocking));
+        g_workers.made[dev] = true;
+    }
+    for (int i = 0; i < kBatchWorkers; ++i) out[i] = g_workers.s[dev][i];
+    return FC_OK;
+}
+}  // namespace
+
 int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
-                     const fc_solve_opts* opts, fc_solve_info* info, void* const* streams) {
-    if (count < 0 || (count > 0 && (!h || !rhs || !u || !info || !streams))) return FC_EINVAL;
+                     const fc_solve_opts* opts, fc_solve_info* info, void* stream) {
+    if (count < 0 || (count > 0 && (!h || !rhs || !u || !info))) return FC_EINVAL;
     for (int i = 0; i < count; ++i) {
         if (!h[i]) return FC_EINVAL;
         for (int j = 0; j < i; ++j)
-            if (h[j] == h[i] || streams[j] == streams[i]) return FC_EINVAL;   // no shared state
+            if (h[j] == h[i]) return FC_EINVAL;   // a handle's workspace serves one solve at a time
     }
+    if (count == 0) return FC_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FC_ECUDA;
+    cudaStream_t ws[kBatchWorkers];
+    if (int rc = worker_streams(dev, ws)) return rc;
+    const int nworkers = std::min(count, kBatchWorkers);
+    // fork: every worker stream starts after the work already queued on the caller's stream
+    cudaStream_t caller = (cudaStream_t)stream;
+    cudaEvent_t fork;
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CK(cudaEventRecord(fork, caller));
+    for (int i = 0; i < nworkers; ++i) CK(cudaStreamWaitEvent(ws[i], fork, 0));
     std::vector<int> rc(count, FC_OK);
     // a bounded pool of host threads takes the problems in order (each solve is a chain of
     // small launches and stream synchronisations: one host thread per solve in flight)
-    const int nworkers = std::min(count, kBatchWorkers);
     std::atomic<int> next{0};
     std::vector<std::thread> workers;
     workers.reserve(nworkers);
     for (int w_ = 0; w_ < nworkers; ++w_)
-        workers.emplace_back([&]() {
+        workers.emplace_back([&, w_]() {
             if (cudaSetDevice(dev) != cudaSuccess) {
                 for (int i; (i = next.fetch_add(1)) < count;) rc[i] = FC_ECUDA;
                 return;
             }
             for (int i; (i = next.fetch_add(1)) < count;) {
-                rc[i] = fc_solve(h[i], &rhs[i], &u[i], opts ? &opts[i] : nullptr, &info[i],
-                                 streams[i]);
-                if (rc[i] != FC_OK && (rc[i] == FC_EINVAL || rc[i] == FC_ERANK ||
-                                       rc[i] == FC_EWORKSPACE || rc[i] == FC_ECUDA))
-                    info[i].status = rc[i];
+                std::memset(&info[i], 0, sizeof(fc_solve_info));
+                rc[i] = fc_solve(h[i], &rhs[i], &u[i], opts ? &opts[i] : nullptr, &info[i], ws[w_]);
+                if (rc[i] != FC_OK && info[i].status == FC_OK) info[i].status = rc[i];
             }
         });
     for (auto& t : workers) t.join();
+    // join: the caller's stream waits for every worker stream
+    int out = FC_OK;
+    for (int i = 0; i < nworkers && out == FC_OK; ++i) {
+        cudaEvent_t done;
+        cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(done, ws[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, done, 0);
+        cudaEventDestroy(done);
+        if (e != cudaSuccess) out = cuda_fail(e);
+    }
+    cudaEventDestroy(fork);
+    if (out != FC_OK) return out;
     for (int i = 0; i < count; ++i)
         if (rc[i] != FC_OK) return rc[i];
     return FC_OK;

@@ -127,6 +127,8 @@ enum {
     D_CR = 11,      // [11..13] rank of the deflated remainder
     D_CT = 14,      // [14..16] combined basis size
     D_C3 = 17,      // [17..19] rank after the final orthonormalisation
+    D_FLAG = 23,    // tensor-core error flag of the handle (bounded wait expired); cleared at
+                    // the entry of each API call, not by the per-truncation reset of [0, D_FLAG)
     D_SIZE = 24
 };
 }  // namespace fc

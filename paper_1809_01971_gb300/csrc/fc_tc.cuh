@@ -41,8 +41,16 @@ constexpr int kTcThreads = 512;     // digit producers (4 per row of the 128-row
 constexpr int kTcBlock = kTcThreads + 32;   // + one warp that issues the MMAs
 constexpr int kTcBadExp = 0x40000000;   // scale marker of a row / column holding Inf or NaN
 
-// Error flag of the tensor-core GEMMs of this translation unit (bounded wait expired).
+// Error flag of the tensor-core GEMMs of this translation unit (bounded wait expired), used
+// when a launch names no flag of its own (a handle passes the flag slot of its workspace).
 static __device__ int g_tc_error;
+// Iteration limit of every bounded mbarrier wait (~1 s of polling).
+constexpr int kTcWaitFull = 1 << 24;
+// Host side (api.cu): the error flag and the producer-side wait limit that the tensor-core
+// launches of the calling thread use.  A handle's calls set the flag to a slot of its own
+// workspace for their duration; the limit is kTcWaitFull unless a test lowered it.
+int* tc_error_target();
+int tc_producer_wait_limit();
 
 FC_DEV uint32_t tc_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -65,9 +73,10 @@ FC_DEV void tc_commit(uint32_t bar) {
                  :: "r"(bar) : "memory");
 }
 
-// Bounded wait for the phase with the given parity of an mbarrier (~1 s at most).
-FC_DEV bool tc_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 24); ++it) {
+// Bounded wait for the phase with the given parity of an mbarrier: at most `limit` polls
+// (kTcWaitFull: ~1 s).  Returns false if the phase did not complete within them.
+FC_DEV bool tc_wait(uint32_t bar, uint32_t parity, int limit = kTcWaitFull) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -348,7 +357,8 @@ template <int BN, class LA, class LB>
 __global__ void __launch_bounds__(kTcBlock, 1)
 gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
                LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
-               int batch, int splits, int kchunk, unsigned long long* work)
+               int batch, int splits, int kchunk, unsigned long long* work, int* err,
+               int wait_limit)
 {
     using Sh = TcShape<BN>;
     constexpr int S = kTcDigits;
@@ -444,7 +454,7 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
             if (st >= 2) {
                 int ok = 1;
                 if (lane == 0)
-                    ok = tc_wait(tc_saddr(&s_bar[buf]), (uint32_t)(((st - 2) >> 1) & 1)) ? 1 : 0;
+                    ok = tc_wait(tc_saddr(&s_bar[buf]), (uint32_t)(((st - 2) >> 1) & 1), wait_limit) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 __syncwarp();                         // the warp's writes follow the wait
                 bad = (ok == 0);
@@ -552,7 +562,7 @@ gemm_tc_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
             atomicAdd(work, (unsigned long long)(S * (S + 1) / 2) * 2ull * kTcBM * BN *
                                 (unsigned long long)(nst * kTcKS));
     } else if (bad && tid == 0) {
-        atomicExch(&g_tc_error, 1);
+        atomicExch(err ? err : &g_tc_error, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -614,25 +624,27 @@ inline bool gemm_tc(cudaStream_t st, int M, int N, int K, LA A, LB B, double alp
     dim3 grid((M + kTcBM - 1) / kTcBM, (N + BN - 1) / BN, batch * splits);
     const bool prof = prof_active(KC_TC);
     unsigned long long* work = prof ? prof_work_counter() : nullptr;
+    int* err = tc_error_target();
+    const int wl = tc_producer_wait_limit();
     ProfMark mark;
     if (prof) prof_begin(st, mark);
     note_launch();
     switch (BN) {
         case 16:
             gemm_tc_kernel<16, LA, LB><<<grid, kTcBlock, TcShape<16>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work, err, wl);
             break;
         case 32:
             gemm_tc_kernel<32, LA, LB><<<grid, kTcBlock, TcShape<32>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work, err, wl);
             break;
         case 48:
             gemm_tc_kernel<48, LA, LB><<<grid, kTcBlock, TcShape<48>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work, err, wl);
             break;
         default:
             gemm_tc_kernel<64, LA, LB><<<grid, kTcBlock, TcShape<64>::SMEM, st>>>(
-                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work);
+                M, N, K, dM, dN, dK, A, B, alpha, beta, C, ldc, bsC, batch, splits, kchunk, work, err, wl);
             break;
     }
     if (prof) prof_end(st, mark);

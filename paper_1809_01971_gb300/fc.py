@@ -58,7 +58,7 @@ class fc_setup_info(C.Structure):
 
 class fc_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("eps", C.c_double), ("kmax", C.c_int),
-                ("max_rank", C.c_int), ("spectral", C.c_int)]
+                ("max_rank", C.c_int), ("spectral", C.c_int), ("precision", C.c_int)]
 
 
 class fc_solve_info(C.Structure):
@@ -101,7 +101,8 @@ def lib() -> C.CDLL:
             "fc_state": (I, [P, cp_p, D, I, cp_p, V]),
             "fc_solve": (I, [P, cp_p, cp_p, C.POINTER(fc_solve_opts), C.POINTER(fc_solve_info), V]),
             "fc_solve_batched": (I, [I, C.POINTER(P), cp_p, cp_p, C.POINTER(fc_solve_opts),
-                                     C.POINTER(fc_solve_info), C.POINTER(V)]),
+                                     C.POINTER(fc_solve_info), V]),
+            "fc_set_wait_limit": (I, [I, C.POINTER(I)]),
             "fc_to_full": (I, [P, cp_p, V, V]),
             "fc_full_solve": (I, [P, V, V, V, V]),
             "fc_destroy": (None, [P]),
@@ -343,11 +344,19 @@ def fc_inner(h: Handle, x: CP, y: CP, stream=None) -> float:
     return out.value
 
 
+def _form(precision):
+    """fc_solve_opts.precision: None -> 0 (the handle's form), else the setup code + 1."""
+    return 0 if precision is None else int(precision) + 1
+
+
 def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0, stream=None,
-             raise_on_fail: bool = True, spectral: bool = False) -> fc_solve_info:
+             raise_on_fail: bool = True, spectral: bool = False, precision=None) -> fc_solve_info:
     """Algorithm 1; spectral=True keeps every iterate in the DST-I eigenbasis (one transform
-    at entry and exit instead of two per mat-vec: the same result)."""
-    o = fc_solve_opts(float(tol), float(eps), int(kmax), int(max_rank), 1 if spectral else 0)
+    at entry and exit instead of two per mat-vec: the same result).  precision: None for the
+    handle's contraction form, else 0 FP64 / 1 double-float / 2 tensor-core digits for this
+    solve."""
+    o = fc_solve_opts(float(tol), float(eps), int(kmax), int(max_rank), 1 if spectral else 0,
+                      _form(precision))
     info = fc_solve_info()
     cr, cu = rhs.desc(), u.desc()
     rc = lib().fc_solve(h.ptr, C.byref(cr), C.byref(cu), C.byref(o), C.byref(info), _stream(stream))
@@ -357,31 +366,39 @@ def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
     return info
 
 
-def fc_solve_batched(handles, rhs, us, streams, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
-                     raise_on_fail: bool = True, spectral: bool = False):
-    """Independent solves run concurrently (a pool of up to 16 host threads, one stream per
-    problem).
-    tol / eps / kmax / max_rank are scalars or per-problem sequences."""
+def fc_solve_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
+                     raise_on_fail: bool = True, spectral: bool = False, precision=None,
+                     stream=None):
+    """Independent solves run concurrently (a pool of up to 16 host threads, each on a worker
+    stream of the library that starts after the work queued on ``stream`` and joins it).
+    tol / eps / kmax / max_rank / precision are scalars or per-problem sequences."""
     count = len(handles)
 
     def per(v):
         return list(v) if isinstance(v, (list, tuple)) else [v] * count
 
-    tols, epss, kms, mrs = per(tol), per(eps), per(kmax), per(max_rank)
+    tols, epss, kms, mrs, prs = per(tol), per(eps), per(kmax), per(max_rank), per(precision)
     H = (C.c_void_p * count)(*[h.ptr.value for h in handles])
     R = (fc_cp * count)(*[x.desc() for x in rhs])
     Uc = (fc_cp * count)(*[x.desc() for x in us])
     O = (fc_solve_opts * count)(*[fc_solve_opts(float(tols[i]), float(epss[i]), int(kms[i]),
-                                                int(mrs[i]), 1 if spectral else 0)
+                                                int(mrs[i]), 1 if spectral else 0, _form(prs[i]))
                                   for i in range(count)])
     infos = (fc_solve_info * count)()
-    S = (C.c_void_p * count)(*[_stream(s) for s in streams])
-    rc = lib().fc_solve_batched(count, H, R, Uc, O, infos, S)
+    rc = lib().fc_solve_batched(count, H, R, Uc, O, infos, _stream(stream))
     for i in range(count):
         us[i].rank = Uc[i].rank
     if raise_on_fail or rc not in (FC_ENOCONV, FC_EBREAKDOWN, FC_ENAN):
         _check("fc_solve_batched", rc)
     return list(infos)
+
+
+def fc_set_wait_limit(iterations: int) -> int:
+    """Test hook: the producer-side wait limit of the tensor-core kernel (fc_set_wait_limit);
+    returns the previous limit."""
+    prev = C.c_int()
+    _check("fc_set_wait_limit", lib().fc_set_wait_limit(int(iterations), C.byref(prev)))
+    return prev.value
 
 
 def fc_to_full(h: Handle, x: CP, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

@@ -302,7 +302,7 @@ def test_solve_config2_3d_n255(fc, problem, precision):
 
 
 def test_solve_batched_matches_independent_solves(fc):
-    """fc_solve_batched runs independent problems concurrently (one stream each); every
+    """fc_solve_batched runs independent problems concurrently (worker streams); every
     result equals the stand-alone fc_solve of the same problem within the solve accuracy,
     and each solves its own equation (full oracle)."""
     rng = np.random.default_rng(fi.seed_for(10))
@@ -311,8 +311,7 @@ def test_solve_batched_matches_independent_solves(fc):
     hs = [fc.fc_setup(p.n, 3, p.alpha, 1.0, p.gamma, p.eps, max_rank=p.max_rank) for p in probs]
     Bs = [fc.CP.from_factors(*p.rhs()) for p in probs]
     Ub = [fc.CP(3, p.n, p.max_rank) for p in probs]
-    streams = [torch.cuda.Stream() for _ in probs]
-    infos = fc.fc_solve_batched(hs, Bs, Ub, streams, tol=[p.tol for p in probs],
+    infos = fc.fc_solve_batched(hs, Bs, Ub, tol=[p.tol for p in probs],
                                 eps=[p.eps for p in probs])
     torch.cuda.synchronize()
     for p, h, B, U, info in zip(probs, hs, Bs, Ub, infos):
@@ -326,7 +325,7 @@ def test_solve_batched_matches_independent_solves(fc):
         assert rel(ub, ref) <= 1e-6 and rel(us, ref) <= 1e-6
         assert rel(ub, us) <= 2.0 * max(rel(ub, ref), rel(us, ref)) + 1e-12
     with pytest.raises(fc.FCError):
-        fc.fc_solve_batched([hs[0], hs[0]], Bs[:2], Ub[:2], streams[:2])
+        fc.fc_solve_batched([hs[0], hs[0]], Bs[:2], Ub[:2])
 
 
 def test_batched_mixed_problems(fc):
@@ -339,8 +338,7 @@ def test_batched_mixed_problems(fc):
                       precision=2) for p in probs]
     Bs = [fc.CP.from_factors(*p.rhs()) for p in probs]
     Us = [fc.CP(p.d, p.n, p.max_rank) for p in probs]
-    streams = [torch.cuda.Stream() for _ in probs]
-    infos = fc.fc_solve_batched(hs, Bs, Us, streams, tol=[p.tol for p in probs],
+    infos = fc.fc_solve_batched(hs, Bs, Us, tol=[p.tol for p in probs],
                                 eps=[p.eps for p in probs], raise_on_fail=False)
     torch.cuda.synchronize()
     worst = 0.0
