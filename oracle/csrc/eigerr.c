@@ -15,6 +15,8 @@
  * two CP tensors is left to a difference of large sums).  g(rho) = a rho^-sn + b rho^sp + c.
  *
  * Factor matrices are row-major n x R per mode (element (i, r) at i*R + r).  d in {2, 3}.
+ * The sums run over the box i_l < m[l] (m[l] <= n; m[l] = n is the whole grid): the caller
+ * accounts for the part outside the box (eigerr.py).  lam holds d blocks of n eigenvalues.
  * Threads: OpenMP over the outermost index.
  */
 #include <math.h>
@@ -34,14 +36,16 @@ static double symbol(double rho, double a, double sn, double b, double sp, doubl
     return v;
 }
 
-int eig_error(int d, int n, const double* lam, double a, double sn, double b, double sp,
-              double c, int Ru, const double* xu, const double* const* Uu, int Rb,
+int eig_error(int d, int n, const int* m, const double* lam, double a, double sn, double b,
+              double sp, double c, int Ru, const double* xu, const double* const* Uu, int Rb,
               const double* xb, const double* const* Ub, int threads, double* out) {
-    if (!(d == 2 || d == 3) || n < 1 || Ru < 0 || Rb < 0 || !out) return -1;
+    if (!(d == 2 || d == 3) || n < 1 || Ru < 0 || Rb < 0 || !out || !m) return -1;
+    for (int l = 0; l < d; ++l)
+        if (m[l] < 0 || m[l] > n) return -1;
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
 #endif
-    const int outer = (d == 3) ? n : 1;
+    const int outer = (d == 3) ? m[2] : 1;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
 #pragma omp parallel reduction(+ : s0, s1, s2)
     {
@@ -50,7 +54,7 @@ int eig_error(int d, int n, const double* lam, double a, double sn, double b, do
 #pragma omp for schedule(dynamic, 1)
         for (int i3 = 0; i3 < outer; ++i3) {
             const double l3 = (d == 3) ? lam[2 * n + i3] : 0.0;
-            for (int i2 = 0; i2 < n; ++i2) {
+            for (int i2 = 0; i2 < m[1]; ++i2) {
                 const double l23 = lam[n + i2] + l3;
                 for (int r = 0; r < Ru; ++r) {
                     double v = xu[r] * Uu[1][(size_t)i2 * Ru + r];
@@ -63,7 +67,7 @@ int eig_error(int d, int n, const double* lam, double a, double sn, double b, do
                     cb[r] = v;
                 }
                 double e0 = 0.0, e1 = 0.0, e2 = 0.0;
-                for (int i1 = 0; i1 < n; ++i1) {
+                for (int i1 = 0; i1 < m[0]; ++i1) {
                     const double* ur = Uu[0] + (size_t)i1 * Ru;
                     const double* br = Ub[0] + (size_t)i1 * Rb;
                     double u = 0.0, bv = 0.0;
