@@ -5,8 +5,9 @@ precond = X -> P(A) X with the fitted inverse symbol,
 trunc   = RHOSVD truncation (oracle.truncate).
 
 Readings: B is column-normalised on entry (same tensor);
-mat-vec outputs are truncated in their Khatri-Rao representation
-(truncate(normalize=False)); X^(0) = 0 so R^(0) = B; "R sufficiently
+every truncation, of mat-vec outputs too, works on the column-normalised
+representation (the RHOSVD of Section 5 with unit columns, the weights
+carrying the norms); X^(0) = 0 so R^(0) = B; "R sufficiently
 small" is the recursive ||R^(k+1)|| / ||B|| <= tol; k_max = 100 (the paper's
 failure threshold for its tables).  The true residual ||B - fun(X)|| / ||B|| is
 reported at exit.
@@ -48,13 +49,13 @@ def pcg(fun_sym, pre_sym, B, eps, tol, max_rank, kmax=100) -> PCGResult:
         return PCGResult(X, 0, 0.0, "ok")
     B = normalise_columns(*B)               # same tensor, unit columns
     R = B                                   # R0 = B - fun(X0), X0 = 0
-    Z = trunc(precond(R), False)            # Z0 = trunc(precond(R0))
+    Z = trunc(precond(R))                   # Z0 = trunc(precond(R0))
     P = Z                                   # P0 = Z0
     rz = cp.inner(R, Z)
     hist = []
     ranks = []
     for k in range(kmax):
-        S = trunc(fun(P), False)            # S = trunc(fun(P))
+        S = trunc(fun(P))                   # S = trunc(fun(P))
         ps = cp.inner(P, S)
         if not ps > 0.0:
             return PCGResult(X, k, hist[-1] if hist else 1.0, "breakdown", hist, ranks)
@@ -66,7 +67,7 @@ def pcg(fun_sym, pre_sym, B, eps, tol, max_rank, kmax=100) -> PCGResult:
         ranks.append(dict(X=cp.rank(X), R=cp.rank(R), S=cp.rank(S), P=cp.rank(P)))
         if rel <= tol:
             return PCGResult(X, k + 1, rel, "ok", hist, ranks)
-        Zn = trunc(precond(R), False)       # Z = trunc(precond(R))
+        Zn = trunc(precond(R))              # Z = trunc(precond(R))
         rzn = cp.inner(R, Zn)
         b = rzn / rz                        # beta_k = <R+,Z+>/<Z,R>
         P = trunc(cp.axpy(Zn, b, P))        # P = trunc(Z + beta P)

@@ -19,10 +19,16 @@ Steps (the paper's order):
 Readings (the paper does not state the thresholds):
   * Side-matrix weighting: W_l = U_l diag(|xi|) with U_l column-normalised and
     xi carrying the term norms, so the singular values are in the units of T.
+    Mat-vec outputs (columns e_k . y_j, not unit) are normalised the same way:
+    the weight of a term is |xi_k eta_j| prod_l ||e_lk . y_lj||.
   * Stage-1 rank: smallest r_l with (sum_{k>r_l} sigma_{l,k}^2)^(1/2)
-    <= eps ||xi||_2 / sqrt(2d), capped at max_tucker = 48.  The CP cap max_rank
-    applies to the canonical terms of stage 2 only, so that in 2D the result
-    is the reduced-SVD (Eckart-Young) truncation the paper names.
+    <= eps ||xi||_2 / sqrt(2d), capped at max_tucker = 48.  ||xi||_2 of the
+    normalised representation is the scale of the RHOSVD error bound
+    (Section 5): projecting mode l costs at most the discarded side-matrix
+    energy times ||M_l||_2, M_l the Khatri-Rao product of the other modes'
+    unit columns.  The CP cap max_rank applies to the canonical terms of
+    stage 2 only, so that in 2D the result is the reduced-SVD (Eckart-Young)
+    truncation the paper names.
   * Stage-2 rank: the canonical terms of step 3 are mutually orthogonal, so
     dropping a set of them costs exactly (sum dropped sigma^2)^(1/2); we drop the
     smallest while that is <= eps ||beta|| / sqrt(2), then keep at most max_rank.
@@ -60,12 +66,8 @@ def truncate(T, eps: float, max_rank: int, info: dict | None = None,
     """trunc(T, eps) of Algorithm 1 (reading above).  Returns a CP tensor with
     orthonormal-slice structure and normalised columns.
 
-    normalize=True rescales every column to unit norm first (weights absorb the
-    norms).  normalize=False keeps the representation as given; the PCG uses it
-    for mat-vec outputs, whose columns are Hadamard products of unit symbol and
-    unit input columns (norm <= 1), which makes the side-matrix Gram a Hadamard
-    product of two small-rank Grams.  Dominating each column of the normalised
-    side matrix, this weighting never keeps fewer directions.
+    normalize=True (what Algorithm 1 uses) rescales every column to unit norm first
+    (weights absorb the norms).  normalize=False keeps the representation as given.
     """
     if normalize:
         xi, U = _normalise(T)
