@@ -1,35 +1,40 @@
 #!/usr/bin/env python
 """Throughput of the low-rank (CP) PCG control solve on one GB300, in 3D control solves/s.
 
-Workload (one step): the six 3D problems d=3, n=255 (16.6M grid points each),
-alpha in {0.25, 0.5, 0.75} x gamma in {1e-1, 1e-3}, beta = 1, right-hand side y_Omega =
-4 seeded separable Gaussians + sin(pi x) sin(2 pi y) sin(3 pi z) (CP rank 5), truncation
-eps = 1e-9, PCG tol = 1e-8, CP rank cap 192 (all six solutions within 1e-6 of the exact one).  Each problem's operator set-up (symbol and
-preconditioner CP factors, workspace) is done once before timing, as a library user
-would for repeated solves with one operator; the timed step is the full Algorithm 1
-(PCG with RHOSVD truncation) for all six right-hand sides.
+Workload (the batching form's configuration): 512 independent 3D problems, n drawn from
+{127, 255, 511, 1023, 2047}, alpha ~ U[0.1, 0.9], gamma log-uniform in [1e-4, 1], beta = 1,
+y_Omega a seeded sum of 1-8 separable Gaussians (fc_inputs.config4), each solved by Algorithm 1
+at the settings that reach relative error 1e-6 (PCG tol 1e-7, truncation eps 1e-8, Tucker ranks
+<= 56, CP ranks <= 256, stall detection after 8 iterations without progress).  Each problem's
+operator set-up (symbol and preconditioner CP factors, workspace) is done once before timing,
+as a library user would for repeated solves with one operator.  One step solves `--batch`
+problems of the set (64 by default: consecutive slices, round robin, so 8 steps cover the 512
+problems; --batch 512 solves the whole set per step) with fc_solve_batched: a pool of 16 host
+threads, each driving one solve at a time on a library worker stream.  Only solves that reach
+the PCG tolerance count toward `value`.
 
-The step runs in each contraction form of the library (fc_setup precision 0: FP64; 1:
-double-float FP32; 2: FP64-accurate digit products on the BF16 tensor cores), and form 2 also
-with the spectral-resident iteration (fc_solve_opts.spectral); `forms` reports all of them,
-and `value` is the fastest whose solutions are all within 1e-6 of the exact one
-(`config.form`), `vs_plain_fp64` its ratio to the FP64 form.
+Contraction forms (fc_solve_opts.precision on the same handles): fp64 (FP64 throughout), df32
+(double-float FP32 contractions), tc64 (FP64-accurate digit products on the BF16 tensor cores)
+and tc64_spectral (tc64 with the iterates kept in the DST-I eigenbasis).  `forms` gives each
+surveyed form's rate over a short run; `value` is the fastest whose surveyed solutions all meet
+the accuracy bound, timed over --warmup + --steps steps; `vs_plain_fp64` is its ratio to fp64.
 
-`value`  : device-resident solves/s (CUDA events on the launching stream, L2 flushed
-           between steps with a 512 MiB write, outside the events).
-`e2e`    : the same through the public API with host buffers, in the reported form: every
-           step copies the right-hand sides from pinned host memory and reads the
-           solutions back.
-Accuracy : after timing, every solution is compared with the library's full-format
-           FP64 eigenbasis solve (16.6M points), and the largest relative L2 error is
-           reported; a run where any form's error exceeds 1e-6 exits non-zero.
-`--impl reference` times the CPU FP64 oracle on the same workload (one problem per
-step, cycling) on this host's cores.
+`value`  : device-resident solves/s (CUDA events on the launching stream; the inputs, 50+ GB
+           of handle tables and workspaces, exceed the 129 MB L2, which is also flushed before
+           every timed step with a 512 MiB write outside the events).
+`e2e`    : the same through the public API with host buffers: every step copies the right-hand
+           sides from pinned host memory and reads the solutions back (min(steps, 3) steps).
+Accuracy : sampled solutions against the library's full-format eigenbasis solve (fast sine
+           transforms; itself pinned to the CPU oracle by the -m gpu tests); the oracle's own
+           check of every form on these workloads is tests/test_gpu_oracle_solve.py.
+`--impl reference` times the CPU FP64 oracle (Algorithm 1 with the oracle's plain quadrature)
+on a bounded sample of the same workload on this host's cores.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -40,23 +45,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "3D control solves/s at rel-err<=1e-6 (CP-PCG, batched; fastest contraction form meeting the bound, vs plain FP64)"
+METRIC = ("3D control solves/s at rel-err<=1e-6 (CP-PCG, batched mixed problems; fastest "
+          "contraction form meeting the bound, vs plain FP64)")
 UNIT = "solves/s"
-WORKLOAD = "3d_n255_6problems_alpha{0.25,0.5,0.75}_gamma{1e-1,1e-3}_rank5rhs_tol1e-8_eps1e-9_cap192"
 L2_FLUSH_BYTES = 512 << 20
+BATCH_SET = 512
+BATCH_STEP = 64
+# stall detection of the solves (fc_solve_opts.stall): a solve whose truncated iterates stop
+# reducing the residual ends after 8 such iterations with its best iterate (FC_ENOCONV)
+STALL = 8
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch", type=int, default=BATCH_STEP,
+                   help="problems per step (slices of the 512-problem set, round robin)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--problems", type=int, default=6)
     p.add_argument("--max-err", type=float, default=1e-6,
-                   help="exit status 3 when a solution's error vs the full solve exceeds this")
-    return p.parse_args()
+                   help="exit status 3 when a sampled solution's error exceeds this")
+    return p.parse_args(argv)
 
 
 def dist_env():
@@ -82,9 +93,16 @@ def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
     return units_per_rank * world / seconds
 
 
-def problems(count):
+def problems(count: int = BATCH_SET):
+    """The batching form's workload: the first `count` problems of fc_inputs.config4."""
     import fc_inputs as fi
-    return [fi.config2(p % 6) for p in range(count)]
+    return [fi.config4(i) for i in range(count)]
+
+
+def workload_name(batch: int) -> str:
+    return (f"3d_mixed_batch_{BATCH_SET}problems_n{{127..2047}}_alpha~U[0.1,0.9]_"
+            f"gamma~logU[1e-4,1]_rank1-8gaussians_tol1e-7_eps1e-8_tucker56_cap256"
+            + ("" if batch >= BATCH_SET else f"_step{batch}"))
 
 
 class ClockSampler:
@@ -135,77 +153,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_solve(prob):
-    """One CP-PCG solve by the CPU FP64 oracle (symbols built as part of the solve)."""
-    from oracle import pcg, quadrature as q
-    fs = q.control_symbol(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, 1e-10)
-    ps = q.precond_symbol(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, 24)
-    return pcg.pcg(fs, ps, prob.rhs(), prob.eps, prob.tol, prob.max_rank)
-
-
-def cpu_baseline(probs, budget_s=25.0):
-    """Oracle solves/s on a bounded sample: whole solves of the workload's problems in order
-    (alpha = 0.25 first, the quickest) until ~budget_s of CPU time has passed."""
-    t0 = time.perf_counter()
-    done = 0
-    while done < len(probs):
-        cpu_oracle_solve(probs[done])
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0))
-    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {done} of the {len(probs)} n=255 3D problems (in workload order, "
-                      f"alpha=0.25 first: the quickest to converge), whole CP-PCG solves incl. "
-                      f"symbol set-up, numpy/scipy FP64 with BLAS threads <= {cores}, {dt:.1f} s"}
-
-
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return 0
-    # one step = one oracle solve of the workload's first problem (alpha = 0.25, gamma = 0.1,
-    # ~10 s on a few cores): a bounded sample, so that the whole run ends in minutes
-    probs = problems(1)
-    for i in range(args.warmup):
-        cpu_oracle_solve(probs[0])
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        cpu_oracle_solve(probs[0])
-    dt = time.perf_counter() - t0
-    v = args.steps / dt
-    cores = len(os.sched_getaffinity(0))
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD,
-                       "step": "one oracle solve of problem 0 (alpha=0.25, gamma=0.1)",
-                       "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle solves of problem 0 of the workload "
-                                       f"(the quickest of the six)"},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-# FP64 peak of the chip from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
-# x 2 flop x 2.07 GHz (an FP64 probe on this part measured 1.19 TFLOP/s at 1.9-2.07 GHz).
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# Dense BF16 tensor throughput of this pool's GB300s, measured and sustained over seconds
-# (cuBLAS 8192^3, MEASURED_PEAKS.json): the tensor-pipe peak of a kernel timed in a long step.
-BF16_PEAK_SUSTAINED_TFLOPS = 1686.8
-# Tensor-core contraction DRAM traffic per launch from one ncu capture; None when not captured
-# for the current kernel.
-TC_TRAFFIC_BYTES = None
-# Eigen-solver DRAM traffic per launch (dram__bytes_read.sum + write) from one ncu capture of
-# the current kernel (3-matrix launch of the n=255 solve); None when not captured for it.
-EIG_TRAFFIC_BYTES = None
-
-
-# (name, fc_setup precision, spectral-resident iteration, dtype, contractions)
+# Forms: (name, fc_solve_opts precision (setup code), spectral-resident, dtype, contractions)
 FORMS = [("fp64", 0, False, "f64", "FP64 throughout"),
          ("df32", 1, False, "f32x2", "large contractions in double-float FP32 (hi+lo); rest FP64"),
          ("tc64", 2, False, "bf16-digits/f64",
@@ -215,10 +163,91 @@ FORMS = [("fp64", 0, False, "f64", "FP64 throughout"),
           "as tc64, iterates kept in the DST-I eigenbasis (one transform at entry and exit)")]
 
 
-def main():
-    args = parse()
+def measured_peaks():
+    """MEASURED_PEAKS.json (HBM copy GB/s, BF16 TFLOP/s burst and sustained) if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# FP32 and FP64 pipe peaks from the unit counts and the maximum SM clock (no measured value
+# exists for either): 152 SMs x 128 FP32 FMA lanes, and 2 FP64 FMA per SM per clock on this
+# part, x 2 flop per FMA x 2.07 GHz.
+def alu_peaks(sm_mhz: float = 2070.0):
+    ghz = sm_mhz / 1e3
+    return {"fp32_tflops": 152 * 128 * 2 * ghz / 1e3, "fp64_tflops": 152 * 2 * 2 * ghz / 1e3}
+
+
+def cpu_oracle_solve(prob):
+    """One CP-PCG solve by the CPU FP64 oracle (its symbols built as part of the solve)."""
+    from oracle import pcg, quadrature as q
+    fs = q.control_symbol(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, 1e-10)
+    ps = q.precond_symbol(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, 24)
+    return pcg.pcg(fs, ps, prob.rhs(), prob.eps, prob.tol, prob.max_rank)
+
+
+def reference_problem(probs):
+    """The bounded CPU sample: the workload's cheapest problem for the oracle (n = 127, the
+    fewest right-hand-side terms)."""
+    small = [p for p in probs if p.n == 127]
+    return min(small, key=lambda p: (len(p.rhs()[0]), p.seed))
+
+
+def cpu_baseline(probs, budget_s=25.0):
+    """Oracle solves/s on a bounded sample: whole solves of the cheapest problem of the
+    workload, repeated until ~budget_s of host time has passed."""
+    prob = reference_problem(probs)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        cpu_oracle_solve(prob)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} whole CP-PCG solves of the workload's cheapest problem "
+                      f"({prob.label}, rank-{len(prob.rhs()[0])} right-hand side) incl. symbol "
+                      f"set-up, numpy/scipy FP64 with BLAS threads <= {cores}, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    probs = problems(BATCH_SET)
+    prob = reference_problem(probs)
+    for i in range(args.warmup):
+        cpu_oracle_solve(prob)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        cpu_oracle_solve(prob)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.batch),
+                       "step": f"one oracle solve of the workload's cheapest problem ({prob.label})",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle solves of {prob.label}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
+    from concurrent.futures import ThreadPoolExecutor
+
     import numpy as np
     import torch
 
@@ -233,26 +262,38 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     main_stream = torch.cuda.current_stream()
-    probs = problems(args.problems)
-    # independent problems: each rank solves the full six-problem set (weak scaling)
+    batch = max(1, min(args.batch, BATCH_SET))
+    probs = problems(BATCH_SET)
+    # one handle per problem (the forms select their contraction per solve), set up in parallel
+    t_setup = time.perf_counter()
+    with ThreadPoolExecutor(16) as ex:
+        hs = list(ex.map(lambda p: fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps,
+                                               max_rank=p.max_rank, max_tucker=p.max_tucker,
+                                               device=dev), probs))
+    t_setup = time.perf_counter() - t_setup
     Bs = [fc.CP.from_factors(*p.rhs(), device=dev) for p in probs]
-    streams = [torch.cuda.Stream(device=dev) for _ in probs]
-    tols = [p.tol for p in probs]
-    epss = [p.eps for p in probs]
+    Us = [fc.CP(p.d, p.n, p.max_rank, device=dev) for p in probs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    slices = [list(range(s, min(s + batch, BATCH_SET))) for s in range(0, BATCH_SET, batch)]
+    counter = {"step": 0}
+
+    def step(form, idx=None):
+        _, prec, spectral, _, _ = FORMS[form]
+        if idx is None:
+            idx = slices[counter["step"] % len(slices)]
+            counter["step"] += 1
+        return fc.fc_solve_batched([hs[i] for i in idx], [Bs[i] for i in idx],
+                                   [Us[i] for i in idx], tol=[probs[i].tol for i in idx],
+                                   eps=[probs[i].eps for i in idx], precision=prec,
+                                   spectral=spectral, stream=main_stream, stall=STALL,
+                                   raise_on_fail=False), idx
 
     def timed(fn):
-        """Device time of fn() from CUDA events: start on the main stream, every problem
-        stream waits on it, and the main stream waits for every problem stream at the end."""
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(main_stream)
-        for s_ in streams:
-            s_.wait_event(e0)
         out = fn()
-        for s_ in streams:
-            main_stream.wait_stream(s_)
         e1.record(main_stream)
         e1.synchronize()
         return e0.elapsed_time(e1), out
@@ -262,180 +303,166 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # accuracy reference: the library's full-format FP64 eigenbasis solve of every problem
-    nn = probs[0].n ** 3
-    full_b = torch.empty(nn, dtype=torch.float64, device=dev)
-    tmp = torch.empty_like(full_b)
-    full_u = []
-    href = [fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps, max_rank=p.max_rank)
-            for p in probs]
-    for p, h, B in zip(probs, href, Bs):
-        fc.fc_to_full(h, B, out=full_b)          # column-major n^3
-        u = torch.empty_like(full_b)
-        fc.fc_full_solve(h, full_b, u, tmp)
-        full_u.append(u)
+    # accuracy sample: three problems of each n <= 1023 class, against the full-format solve
+    sample = []
+    for nn in (127, 255, 511, 1023):
+        sample += [i for i, p in enumerate(probs) if p.n == nn][:3]
+
+    def sample_errors():
+        worst = 0.0
+        for i in sample:
+            p, h = probs[i], hs[i]
+            b = torch.empty(p.n ** 3, dtype=torch.float64, device=dev)
+            fc.fc_to_full(h, Bs[i], out=b)
+            u = torch.empty_like(b)
+            fc.fc_full_solve(h, b, u, u)
+            fc.fc_to_full(h, Us[i], out=b)
+            worst = max(worst, float(torch.linalg.norm(b - u) / torch.linalg.norm(u)))
+            del b, u
+        return worst
 
     sampler = ClockSampler(local)
     sampler.start()
-    results = {}
-    handles = {0: href}
-    for form, (fname, prec, spectral, _, _) in enumerate(FORMS):
-        if prec not in handles:
-            handles[prec] = [fc.fc_setup(p.n, p.d, p.alpha, p.beta, p.gamma, p.eps,
-                                         max_rank=p.max_rank, precision=prec) for p in probs]
-        hs = handles[prec]
-        Us = [fc.CP(p.d, p.n, p.max_rank, device=dev) for p in probs]
-
-        def step(hs=hs, Us=Us, spectral=spectral):
-            # the step's problems run concurrently, one stream each (fc_solve_batched)
-            return fc.fc_solve_batched(hs, Bs, Us, tol=tols, eps=epss, spectral=spectral,
-                                       stream=main_stream)
-
-        for _ in range(args.warmup):
-            step()
-        barrier()
-        fc.fc_prof_enable(fc.fc.PROF_JACOBI)
-        launches0 = fc.fc_launch_count()
-        times, iters = [], []
-        for _ in range(args.steps):
-            ms, infos = timed(step)
-            times.append(ms)
-            iters.append([i.iters for i in infos])
-        launches = fc.fc_launch_count() - launches0
-        prof = fc.fc_prof_read()
-        barrier()
-        t_total = max_over_ranks(sum(times) / 1e3, world, dev)
-        err = 0.0
-        for h, U, u in zip(hs, Us, full_u):
-            fc.fc_to_full(h, U, out=tmp)
-            err = max(err, float(torch.linalg.norm(tmp - u) / torch.linalg.norm(u)))
-        tc_prof = None
-        if fname == "tc64":
-            # the tensor-core contraction class, instrumented over extra (untimed) steps
-            fc.fc_prof_enable(fc.fc.PROF_TC)
-            tc_times = [timed(step)[0] for _ in range(args.steps)]
-            tc_prof = fc.fc_prof_read() + (sum(tc_times),)
-            barrier()
-        results[form] = {"hs": hs, "Us": Us, "step": step, "t_total": t_total,
-                         "value": job_rate(len(probs) * args.steps, world, t_total),
-                         "launches": launches, "prof": prof, "iters": iters[-1], "err": err,
-                         "tc_prof": tc_prof}
+    # survey: every form over the sample problems and one batch (short run, after a warm-up)
+    survey = {}
+    for f in (3, 2, 1, 0):
+        step(f, sample)
+        ms_s, (infos_s, _) = timed(lambda: step(f, sample))
+        err = sample_errors()
+        ms_b, (infos_b, idx) = timed(lambda: step(f, slices[0]))
+        ok = all(i.status == 0 for i in infos_s)
+        conv = sum(1 for i in infos_b if i.status == 0)
+        survey[f] = {"value": job_rate(conv, world, max_over_ranks(ms_b / 1e3, world, dev)),
+                     "unit": UNIT, "ms_per_step": ms_b, "steps": 1,
+                     "max_rel_err_vs_full_sample": err, "sample_converged": ok,
+                     "converged": f"{conv}/{len(idx)}",
+                     "pcg_iters_mean": float(np.mean([i.iters for i in infos_b])),
+                     "contractions": FORMS[f][4]}
+    meets = [f for f in survey if survey[f]["sample_converged"] and
+             survey[f]["max_rel_err_vs_full_sample"] <= args.max_err]
+    best = max(meets, key=lambda f: survey[f]["value"]) if meets else 0
+    # the headline: warm-up and exactly K timed steps of the chosen form
+    counter["step"] = 0
+    for _ in range(args.warmup):
+        step(best)
+    barrier()
+    launches0 = fc.fc_launch_count()
+    times, iters, statuses = [], [], []
+    for _ in range(args.steps):
+        ms, (infos, idx) = timed(lambda: step(best))
+        times.append(ms)
+        iters += [i.iters for i in infos]
+        statuses += [i.status for i in infos]
+    launches = fc.fc_launch_count() - launches0
+    barrier()
     clocks = sampler.stop()
-
-    ok = [f for f in results if results[f]["err"] <= args.max_err]
-    best = max(ok, key=lambda f: results[f]["value"]) if ok else 0
-    R = results[best]
-    value, t_total = R["value"], R["t_total"]
-    solves = len(probs) * args.steps * world
-
-    # the FP64 problems one after another on one stream (context for the batched number)
-    hs0, Us0 = results[0]["hs"], results[0]["Us"]
-
-    def step_sequential():
-        return [fc.fc_solve(h, B, U, tol=p.tol, eps=p.eps, stream=main_stream)
-                for p, h, B, U in zip(probs, hs0, Bs, Us0)]
-
-    seq_steps = max(1, args.steps // 2)
-    seq_ms = sum(timed(step_sequential)[0] for _ in range(seq_steps))
-    seq_value = len(probs) * seq_steps / (seq_ms / 1e3)
+    t_total = max_over_ranks(sum(times) / 1e3, world, dev)
+    solved = sum(1 for s_ in statuses if s_ == 0)           # converged solves only
+    value = job_rate(solved, world, t_total)
+    err_best = sample_errors()
 
     # end to end through the public API with host buffers, in the reported form
-    hsb, Usb = R["hs"], R["Us"]
-    host_in = []
-    for p in probs:
-        xi, U = p.rhs()
-        host_in.append((torch.tensor(xi).pin_memory(),
-                        torch.tensor(np.stack([u.T for u in U])).pin_memory()))
+    host_in = [(torch.tensor(p.rhs()[0]).pin_memory(),
+                torch.tensor(np.stack([u.T for u in p.rhs()[1]])).pin_memory()) for p in probs]
     host_out = [(torch.empty(p.max_rank, dtype=torch.float64).pin_memory(),
-                 torch.empty(p.d, p.max_rank, p.n, dtype=torch.float64).pin_memory()) for p in probs]
-    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_in)
-    d2h = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_out)
+                 torch.empty(p.d, p.max_rank, p.n, dtype=torch.float64).pin_memory())
+                for p in probs]
 
-    def e2e_step():
-        for (xi_h, U_h), p, B, s_ in zip(host_in, probs, Bs, streams):
+    def e2e_step(idx):
+        for i in idx:
+            xi_h, U_h = host_in[i]
             R_ = xi_h.numel()
-            with torch.cuda.stream(s_):
-                B.xi[:R_].copy_(xi_h, non_blocking=True)
-                B.U[:, :R_, :p.n].copy_(U_h, non_blocking=True)
-            B.rank = R_
-        fc.fc_solve_batched(hsb, Bs, Usb, tol=tols, eps=epss, spectral=FORMS[best][2],
-                            stream=main_stream)
-        for (xo, Uo), p, U, s_ in zip(host_out, probs, Usb, streams):
-            with torch.cuda.stream(s_):
-                xo.copy_(U.xi[:p.max_rank], non_blocking=True)
-                Uo.copy_(U.U[:, :p.max_rank, :p.n], non_blocking=True)
+            Bs[i].xi[:R_].copy_(xi_h, non_blocking=True)
+            Bs[i].U[:, :R_, :probs[i].n].copy_(U_h, non_blocking=True)
+            Bs[i].rank = R_
+        out = step(best, idx)
+        for i in idx:
+            xo, Uo = host_out[i]
+            xo.copy_(Us[i].xi[:probs[i].max_rank], non_blocking=True)
+            Uo.copy_(Us[i].U[:, :probs[i].max_rank, :probs[i].n], non_blocking=True)
+        return out
 
-    timed(e2e_step)
-    e2e_times = []
+    n_e2e = max(1, min(args.steps, 3))
+    e2e_step(slices[0])
     barrier()
-    for _ in range(args.steps):
-        e2e_times.append(timed(e2e_step)[0])
+    e2e_ms = [timed(lambda s=s: e2e_step(slices[s % len(slices)]))[0] for s in range(n_e2e)]
     barrier()
-    e2e_value = job_rate(len(probs) * args.steps, world, max_over_ranks(sum(e2e_times) / 1e3, world, dev))
+    e2e_solved = sum(len(slices[s % len(slices)]) for s in range(n_e2e))
+    e2e_value = job_rate(e2e_solved, world, max_over_ranks(sum(e2e_ms) / 1e3, world, dev))
+    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_in) * e2e_solved // BATCH_SET
+    d2h = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_out) * e2e_solved // BATCH_SET
 
-    roofline = None
-    jac_n, jac_ms, jac_work = R["prof"]
-    if jac_n > 0 and jac_ms > 0:
-        achieved = jac_work / jac_n / (jac_ms / jac_n * 1e-3) / 1e12     # TFLOP/s
-        peak = FP64_PEAK_GFLOPS / 1e3
-        roofline = {"kernel": "gjacobi_kernel (graded eigen-solves of the RHOSVD: FP32 Jacobi "
-                              "sweeps, FP64 orthonormalisation)",
-                    "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": EIG_TRAFFIC_BYTES,
-                    "peak_kind": "FP64, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
-                    "work": "9 c^3 flop per c x c matrix (textbook dense eigen-solve count)",
-                    "launches": jac_n, "avg_launch_us": 1e3 * jac_ms / jac_n,
-                    "event_ms_over_step_ms": jac_ms / (t_total * 1e3),
-                    "note": "launches overlap across the problem streams, so summed event time can exceed step time"}
-    roofline_tc = None
-    if results[2]["tc_prof"] and results[2]["tc_prof"][0] > 0:    # FORMS[2] = tc64
-        tn, tms, twork, tstep_ms = results[2]["tc_prof"]
-        achieved = twork / tn / (tms / tn * 1e-3) / 1e12
-        peak = BF16_PEAK_SUSTAINED_TFLOPS
-        roofline_tc = {"kernel": "gemm_tc_kernel (FP64 contractions of the tc64 form as BF16 "
-                                 "digit-pair MMAs on tcgen05, TMEM accumulators)",
-                       "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": TC_TRAFFIC_BYTES,
-                       "peak_kind": "measured BF16 dense, sustained (MEASURED_PEAKS.json)",
-                       "work": "BF16 MMA flops issued: 36 digit pairs x 2 x 128 x N_tile per K",
-                       "launches": tn, "avg_launch_us": 1e3 * tms / tn,
-                       "event_ms_over_step_ms": tms / tstep_ms}
+    # roofline of the full-format solve kernel (fast sine transforms), timed here on its own
+    roofline = full_solve_roofline(fc, torch, dev, main_stream)
     if rank == 0:
         name, _, _, dtype, what = FORMS[best]
-        forms = {FORMS[f][0]: {"value": results[f]["value"], "unit": UNIT,
-                               "ms_per_step": 1e3 * results[f]["t_total"] / args.steps,
-                               "max_rel_err_vs_full": results[f]["err"],
-                               "pcg_iters": results[f]["iters"],
-                               "gpu_launches": int(results[f]["launches"]),
-                               "contractions": FORMS[f][4]} for f in results}
+        forms = {FORMS[f][0]: survey[f] for f in sorted(survey)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-                "config": {"workload": WORKLOAD, "problems_per_step": len(probs),
+                "config": {"workload": workload_name(batch), "problems_per_step": batch,
                            "form": name,
-                           "l2": "flushed between steps (512 MiB write, untimed)",
-                           "setup": "per operator, before timing",
-                           "concurrency": "fc_solve_batched: one stream per problem, up to 16 host threads",
-                           "work_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"),
-                           "pcg_iters": R["iters"]},
+                           "l2": "inputs > L2 (50+ GB of tables and workspaces); also flushed "
+                                 "before every timed step (512 MiB write, untimed)",
+                           "setup": f"per problem, before timing ({t_setup:.0f} s, 16 threads)",
+                           "concurrency": "fc_solve_batched: 16 host threads, 16 library "
+                                          "worker streams",
+                           "work_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8")},
                 "forms": forms,
-                "vs_plain_fp64": value / results[0]["value"],
-                "sequential_fp64_value": seq_value,
-                "max_rel_err_vs_full": R["err"],
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
-                "gpu_launches": int(R["launches"]),
+                "vs_plain_fp64": value / survey[0]["value"] if survey[0]["value"] else None,
+                "pcg_iters_mean": float(np.mean(iters)) if iters else None,
+                "solves_timed": len(statuses),
+                "solves_converged": solved // max(world, 1) if world > 1 else solved,
+                "max_rel_err_vs_full_sample": err_best,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
+                        "d2h_bytes_per_step": d2h // n_e2e},
+                "gpu_launches": int(launches),
                 "clocks": clocks,
                 "roofline": roofline,
-                "roofline_tc": roofline_tc,
                 "cpu_baseline": None}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(probs)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-    return 0 if all(results[f]["err"] <= args.max_err for f in results) else 3
+    return 0 if err_best <= args.max_err else 3
+
+
+def full_solve_roofline(fc, torch, dev, stream, n=1023):
+    """The full-format eigenbasis solve at n = 1023 (1.07e9 points): 2d - 1 = 5 passes of fast
+    sine transforms, each reading and writing the array once (80 n^3 bytes), timed with CUDA
+    events over 3 solves after 1 warm-up on the launching stream."""
+    peaks = measured_peaks()
+    h = fc.fc_setup(n, 3, 0.5, 1.0, 1e-3, 1e-8, device=dev)
+    b = torch.randn(n ** 3, dtype=torch.float64, device=dev)
+    u = torch.empty_like(b)
+    fc.fc_full_solve(h, b, u, u, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        fc.fc_full_solve(h, b, u, u, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    bytes_ = 80.0 * n ** 3
+    achieved = bytes_ / (ms * 1e-3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64 = alu_peaks()["fp64_tflops"]
+    # 6 transforms of n^2 lines (the middle pass transforms twice), 5 N log2 N flop per line
+    flops = 6 * n ** 2 * 5.0 * (n + 1) * math.log2(n + 1) / 1e12
+    del b, u
+    return {"kernel": "dst_pass_kernel (full-format solve, n=1023: 5 passes of FP64 FFT-based "
+                      "DST-I lines, division by g fused into the middle pass)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_kind": "measured HBM copy (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks
+                         else "fallback 6.8 TB/s",
+            "work": "80 n^3 bytes per solve (5 passes x read + write of 8 n^3 bytes)",
+            "ms_per_solve": ms,
+            "fp64_alu_frac": flops / (ms * 1e-3) / fp64,
+            "note": "FP64 FFTs on this part are bound by its FP64 pipe (~1.26 TFLOP/s), not HBM"}
 
 
 if __name__ == "__main__":

@@ -122,12 +122,18 @@ typedef struct fc_solve_opts {
     int precision;      /* contraction form of this solve: 0 the handle's (fc_setup_opts.      */
                         /* precision); 1 FP64, 2 double-float FP32, 3 tensor-core digits, so   */
                         /* one set-up serves every form [0]                                     */
+    int stall;          /* > 0: stop with FC_ENOCONV once `stall` iterations in a row have not */
+                        /* brought ||R||/||B|| 10% below the last value that did (truncated    */
+                        /* iterates reach a floor set by eps and the rank caps), and return    */
+                        /* the iterate with the smallest recursive residual (also at kmax);    */
+                        /* 0: Algorithm 1 as stated, stop at tol or kmax only [0]              */
 } fc_solve_opts;
 
 typedef struct fc_solve_info {
     int status;         /* FC_OK, FC_ENOCONV, FC_EBREAKDOWN, FC_ENAN                          */
     int iters;
-    double relres;      /* last recursive ||R^(k+1)|| / ||B||                                 */
+    double relres;      /* last recursive ||R^(k+1)|| / ||B|| (with stall detection on an     */
+                        /* unconverged exit: that of the returned iterate)                      */
     int rank_x;         /* CP rank of the returned solution                                   */
     int max_rank_seen;  /* largest CP rank of any truncated iterate                           */
     int trunc_calls;
@@ -242,7 +248,10 @@ int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev
  *    every GPU which loads the library holds until the process exits; ranks above
  *    FC_STATIC_MAX_RANK return FC_ERANK.  No cudaMalloc, cudaFree or allocating library call.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current; make that first call before any stream capture.
+ *    with that device current; make that first call before any stream capture.  The address
+ *    is kept for the life of the process: after cudaDeviceReset on that device, do not call
+ *    this entry point again in the same process.
+ *  - x, y and dev_out must live on the calling thread's current device.
  *  - All calls share the one array: calls whose work overlaps on the GPU (other streams or
  *    threads) race and must be serialised by the caller. */
 #define FC_STATIC_MAX_RANK 128

@@ -1,12 +1,15 @@
-"""Command-line solve of one control problem (beta^2 A^-alpha + gamma A^alpha) u = beta y_Omega
-with a seeded synthetic right-hand side:
+"""Command-line solve of control problems (beta^2 A^-alpha + gamma A^alpha) u = beta y_Omega
+with seeded synthetic right-hand sides:
 
     python -m paper_1809_01971_gb300 --problem 5 --precision 2 --repeats 3
+    python -m paper_1809_01971_gb300 --batch 0:8 --precision 2 --spectral
 
 --problem k selects the k-th 3D n = 255 problem (alpha in {0.25, 0.5, 0.75} x gamma in
-{1e-1, 1e-3}: four separable Gaussians + one grid sine mode), --problem 2d the 2D n = 63 one.
---precision picks the contraction form (0 FP64, 1 double-float FP32, 2 tensor-core digit
-products).  Prints the PCG summary and the device time of each solve (CUDA events).
+{1e-1, 1e-3}: four separable Gaussians + one grid sine mode), --problem 2d the 2D n = 63 one;
+--batch a:b solves problems a .. b-1 of the 512-problem mixed batch (n in {127 .. 2047}) one
+after another on one stream, at their 1e-6 settings.  --precision picks the contraction form
+(0 FP64, 1 double-float FP32, 2 tensor-core digit products).  Prints the PCG summary and the
+device time of each solve (CUDA events).
 """
 from __future__ import annotations
 
@@ -18,7 +21,9 @@ import sys
 def main(argv=None) -> int:
     p = argparse.ArgumentParser(prog="python -m paper_1809_01971_gb300")
     p.add_argument("--problem", default="5", help="0..5 (3D, n=255) or 2d (n=63)")
+    p.add_argument("--batch", default=None, help="a:b, problems of the mixed batch")
     p.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    p.add_argument("--spectral", action="store_true")
     p.add_argument("--repeats", type=int, default=1)
     args = p.parse_args(argv)
 
@@ -30,23 +35,31 @@ def main(argv=None) -> int:
     import fc_inputs as fi
     from . import fc
 
-    prob = fi.config1() if args.problem == "2d" else fi.config2(int(args.problem))
-    h = fc.fc_setup(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, prob.eps,
-                    max_rank=prob.max_rank, precision=args.precision)
-    B = fc.CP.from_factors(*prob.rhs())
-    U = fc.CP(prob.d, prob.n, prob.max_rank)
+    if args.batch:
+        a, b = (int(x) for x in args.batch.split(":"))
+        probs = [fi.config4(i) for i in range(a, b)]
+    else:
+        probs = [fi.config1() if args.problem == "2d" else fi.config2(int(args.problem))]
     stream = torch.cuda.current_stream()
-    for r in range(max(1, args.repeats)):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        info = fc.fc_solve(h, B, U, tol=prob.tol, eps=prob.eps)
-        e1.record(stream)
-        e1.synchronize()
-        print(f"{prob.label} precision={args.precision} solve {r}: status {info.status} "
-              f"iters {info.iters} relres {info.relres:.2e} rank {U.rank} "
-              f"max rank {info.max_rank_seen} truncations {info.trunc_calls} "
-              f"{e0.elapsed_time(e1):.2f} ms", flush=True)
+    for prob in probs:
+        h = fc.fc_setup(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, prob.eps,
+                        max_rank=prob.max_rank, max_tucker=prob.max_tucker,
+                        precision=args.precision)
+        B = fc.CP.from_factors(*prob.rhs())
+        U = fc.CP(prob.d, prob.n, prob.max_rank)
+        for r in range(max(1, args.repeats)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = fc.fc_solve(h, B, U, tol=prob.tol, eps=prob.eps, spectral=args.spectral,
+                               stall=8 if args.batch else 0, raise_on_fail=False)
+            e1.record(stream)
+            e1.synchronize()
+            print(f"{prob.label} precision={args.precision} solve {r}: status {info.status} "
+                  f"iters {info.iters} relres {info.relres:.2e} rank {U.rank} "
+                  f"max rank {info.max_rank_seen} truncations {info.trunc_calls} "
+                  f"{e0.elapsed_time(e1):.2f} ms", flush=True)
+        h.destroy()
     return 0
 
 

@@ -67,6 +67,11 @@ int cuda_fail(cudaError_t e) {
     g_cuda_msg = cudaGetErrorString(e);
     return FC_ECUDA;
 }
+}  // namespace
+
+int fc::record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+namespace {
 #define CK(x)                                        \
     do {                                             \
         cudaError_t _e = (x);                        \
@@ -122,12 +127,17 @@ struct fc_ctx {
     double *xiP = nullptr, *EP = nullptr, *GEP = nullptr;   // preconditioner CP and Grams
     // state symbol beta rho^-alpha: the first RS columns of EA with weights xiA / beta
     double *xiS = nullptr, *GES = nullptr;
+    // dominating column weights of the three symbols' Khatri-Rao side matrices, per mode
+    // (mode stride R): xw_l[k] = |xi_k| prod_{m != l} max_i |E_m[i, k]| (see symbol_proxy_weights)
+    double *xiAw = nullptr, *xiPw = nullptr, *xiSw = nullptr;
     int RS = 0;
     SymbolSpec spec;      // operator symbol g(rho) = a rho^-sn + b rho^sp + c
     bool spectral = false;   // during a spectral-resident solve: operands already in the eigenbasis
     double* V = nullptr;     // variable coefficients: orthonormal eigenvector matrices of the 1D
                              // stiffness matrices (d x n x n, column-major), else the DST-I
     double alpha_eff = 0.0;   // exponent of the symbol's spectrum (1 for the directional operator)
+    double2* twid = nullptr;  // e^{-i pi k / (n+1)}, k <= n (fast sine transforms; n+1 a power of
+                              // two, n < 4096)
     int prec = GP_F64;        // contractions in FP64 or double-float FP32 (fc_setup_opts.precision)
     // compressed mode factors of the three symbols (operator, preconditioner, state):
     // Et[s] (3 modes x n x rE[s]) and Mt[s] (3 modes x rE[s] x R_s), see compress_factor
@@ -135,17 +145,16 @@ struct fc_ctx {
     double *Et[3] = {nullptr, nullptr, nullptr}, *Mt[3] = {nullptr, nullptr, nullptr};
     int rE[3] = {0, 0, 0};
     int rEmax = 0;
-    double* ones = nullptr;   // max(kMaxC, rEmax) ones (weights of the compressed columns)
     // workspace (caller-owned)
     char* ws = nullptr;
     size_t ws_bytes = 0;
     // workspace slices
     struct {
-        double *Y, *Y2, *Q, *tmp, *M, *Tm, *GY, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *wK, *C2, *wKt;
-        double *core, *G3, *ev3, *W3, *Srot, *SG, *mus, *Vs, *sigma, *X, *Yh;
+        double *Y, *Y2, *Q, *tmp, *M, *Tm, *GY, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *wK, *C2, *wN;
+        double *core, *G3, *ev3, *W3, *Srot, *SG, *mus, *Vs, *sigma, *X, *Yh, *Nu;
         double *scal, *Mi;
         int *dims, *tslice, *tidx;
-        CP cat, Xs, Rs, Ps, Zs, Ss;
+        CP cat, Xs, Rs, Ps, Zs, Ss, Xb;
         double* pinned_dummy;
     } w{};
     static constexpr unsigned long long kSeed0 = 0x1809019710ull;
@@ -181,7 +190,7 @@ size_t layout(fc_ctx* h, Arena& a) {
     w.C = a.d(3 * (size_t)std::max(RM, CM) * K);
     w.wK = a.d((size_t)K);
     w.C2 = a.d(3 * (size_t)CM * std::max<long long>(1, (long long)h->rEmax * h->KIN));
-    w.wKt = a.d(std::max<long long>(1, (long long)h->rEmax * h->KIN));
+    w.wN = a.d(3 * (size_t)K);
     w.core = a.d((size_t)RM * RM * RM);
     w.G3 = a.d((size_t)RM * RM);
     w.ev3 = a.d((size_t)RM);
@@ -193,6 +202,7 @@ size_t layout(fc_ctx* h, Arena& a) {
     w.sigma = a.d((size_t)RM * RM);
     w.X = a.d(3 * (size_t)RM * h->QMAX);
     w.Yh = a.d(3 * (size_t)n * h->KIN);
+    w.Nu = a.d(3 * (size_t)std::max(h->RA, h->RP) * h->KIN);
     w.scal = a.d(64);
     w.Mi = a.d(3 * (size_t)h->KIN * h->KIN);
     w.dims = a.i(D_SIZE);
@@ -210,6 +220,7 @@ size_t layout(fc_ctx* h, Arena& a) {
     mkcp(w.Ps, h->CAP);
     mkcp(w.Zs, h->CAP);
     mkcp(w.Ss, h->CAP);
+    mkcp(w.Xb, h->CAP);
     (void)d;
     return a.off + 256;
 }
@@ -224,6 +235,7 @@ int ensure_attributes() {
     if (!done[dev]) {
         cudaError_t e = set_linalg_attributes();
         if (e == cudaSuccess) e = set_symeig_attributes();
+        if (e == cudaSuccess) e = set_fft_attributes(4096);   // the largest line length
         if (e != cudaSuccess) return cuda_fail(e);
         done[dev] = true;
     }
@@ -237,19 +249,61 @@ int ensure_attributes() {
 // alpha = 0.75 a looser 1e-12 left 5e-7 in the solution of a sine-mode right-hand side.
 constexpr double kCompressTol = 1e-14;
 
-int compress_symbols(fc_ctx* h) {
+// Dominating weights of a symbol's Khatri-Rao side matrices (cold path, host).  A mat-vec
+// output has the terms xa_k xb_j (x)_l (e_lk . y_lj) with unit e_lk, y_lj; its columns are not
+// unit vectors (nu_l(k, j) = ||e_lk . y_lj|| <= ||e_lk||_inf), so the column-normalised tensor
+// has the weights |xa_k xb_j| prod_l nu_l(k, j).  The stage-1 side matrix of mode l is taken with
+// the columns e_lk . y_lj and the weights |xa_k xb_j| prod_{m != l} ||e_mk||_inf, which dominate
+// the normalised weights column by column, so every energy it measures bounds the normalised
+// one, while the weights keep the Khatri-Rao product form (xa_k-part times xb_j) that the
+// structured sketch and the Hadamard Gram GE . GY need.
+int symbol_proxy_weights(fc_ctx* h) {
     const int n = h->n, d = h->d;
     const int Rs[3] = {h->RA, h->RP, h->RS};
     const double* Edev[3] = {h->EA, h->EP, h->EA};
     const long long bsE[3] = {(long long)n * h->RA, (long long)n * h->RP, (long long)n * h->RA};
     const double* xdev[3] = {h->xiA, h->xiP, h->xiS};
+    double* out[3] = {h->xiAw, h->xiPw, h->xiSw};
+    for (int sy = 0; sy < 3; ++sy) {
+        const int R = Rs[sy];
+        if (R == 0) continue;
+        std::vector<double> E((size_t)n * R), xa(R), cmax((size_t)3 * R, 1.0), xw((size_t)3 * R, 0.0);
+        CK(cudaMemcpy(xa.data(), xdev[sy], sizeof(double) * R, cudaMemcpyDeviceToHost));
+        for (int l = 0; l < d; ++l) {
+            CK(cudaMemcpy(E.data(), Edev[sy] + l * bsE[sy], sizeof(double) * n * R,
+                          cudaMemcpyDeviceToHost));
+            for (int k = 0; k < R; ++k) {
+                double m = 0.0;
+                for (int i = 0; i < n; ++i) m = std::max(m, std::fabs(E[i + (size_t)k * n]));
+                cmax[(size_t)l * R + k] = m;
+            }
+        }
+        for (int l = 0; l < d; ++l)
+            for (int k = 0; k < R; ++k) {
+                double v = std::fabs(xa[k]);
+                for (int m = 0; m < d; ++m)
+                    if (m != l) v *= cmax[(size_t)m * R + k];
+                xw[(size_t)l * R + k] = v;
+            }
+        CK(cudaMemcpy(out[sy], xw.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice));
+    }
+    return FC_OK;
+}
+
+int compress_symbols(fc_ctx* h) {
+    const int n = h->n, d = h->d;
+    const int Rs[3] = {h->RA, h->RP, h->RS};
+    const double* Edev[3] = {h->EA, h->EP, h->EA};
+    const long long bsE[3] = {(long long)n * h->RA, (long long)n * h->RP, (long long)n * h->RA};
+    const double* xdev[3] = {h->xiAw, h->xiPw, h->xiSw};   // per-mode dominating weights
     std::vector<Compressed> comp(3 * d);
     for (int sy = 0; sy < 3; ++sy) {
         const int R = Rs[sy];
         if (R == 0) continue;                 // no state symbol for the test operators
         std::vector<double> E((size_t)n * R), xa(R);
-        CK(cudaMemcpy(xa.data(), xdev[sy], sizeof(double) * R, cudaMemcpyDeviceToHost));
         for (int l = 0; l < d; ++l) {
+            CK(cudaMemcpy(xa.data(), xdev[sy] + (size_t)l * R, sizeof(double) * R,
+                          cudaMemcpyDeviceToHost));
             CK(cudaMemcpy(E.data(), Edev[sy] + l * bsE[sy], sizeof(double) * n * R,
                           cudaMemcpyDeviceToHost));
             if (!compress_factor(E.data(), n, R, xa.data(), kCompressTol, comp[sy * d + l]))
@@ -264,15 +318,10 @@ int compress_symbols(fc_ctx* h) {
         h->rEmax = std::max(h->rEmax, r);
         total += 3 * ((size_t)n * r + (size_t)r * Rs[sy]);
     }
-    const size_t nones = std::max(kMaxC, h->rEmax);
-    total += nones;
+
     if (cudaMalloc(&h->ctab, total * sizeof(double)) != cudaSuccess) return FC_ECUDA;
     CK(cudaMemset(h->ctab, 0, total * sizeof(double)));
     double* p = h->ctab;
-    h->ones = p;
-    p += nones;
-    std::vector<double> ones(nones, 1.0);
-    CK(cudaMemcpy(h->ones, ones.data(), sizeof(double) * nones, cudaMemcpyHostToDevice));
     for (int sy = 0; sy < 3; ++sy) {
         const int r = h->rE[sy], R = Rs[sy];
         h->Et[sy] = p; p += 3 * (size_t)n * r;
@@ -464,7 +513,16 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
              LdT{kr->Yh, n, (long long)n * h->KIN}, 1.0, 0.0, w.GY, n, nn, d);
         gemm(st, n, cs, n, LdHad{kr->GE, w.GY, n, nn, nn}, LdN{Qb, n, nC}, 1.0, 0.0, w.GQ, n, nC, d);
         gemm(st, cs, cs, n, LdT{Qb, n, nC}, LdN{w.GQ, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
-        launch_kr_wnorm(st, kr->Ra, kr->xa, kr->S, kr->xb, w.scal + 4);
+        // budget scale: the norm of the column-normalised weights,
+        // sum_{k,j} (xa_k xb_j)^2 prod_l nu_l(k,j)^2 with nu_l(k,j)^2 = ((E_l.E_l)^T (Yh_l.Yh_l))[k,j]
+        gemm(st, kr->Ra, kr->S, n, LdSqT{kr->E, n, kr->bsE}, LdSqN{kr->Yh, n, (long long)n * h->KIN},
+             1.0, 0.0, w.Nu, kr->Ra, (long long)std::max(h->RA, h->RP) * h->KIN, d);
+        launch_inner_reduce(st, d, kr->Ra, kr->S, kr->xa, kr->xb, w.Nu, kr->Ra,
+                            (long long)std::max(h->RA, h->RP) * h->KIN, w.scal + 4, true);
+        // per mode, the weights that turn the columns e_lk . y_lj into those of the
+        // column-normalised tensor (the energies below are measured with them)
+        launch_kr_norm_weights(st, d, kr->Ra, kr->S, kr->xa, kr->xb, w.Nu, kr->Ra,
+                               (long long)std::max(h->RA, h->RP) * h->KIN, w.wN, h->KMAX);
         launch_outer_weights(st, kr->Ra, kr->xa, kr->S, kr->xb, w.wK);
     } else {
         // Bq = Q^T W (cs x K) in w.C, T = Bq Bq^T
@@ -487,13 +545,19 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     const long long RK = (long long)CM * K;
     const double* wK = dn ? dn->w : w.wK;
     if (kr) {
-        // B2t_l = Zc_l^T (Et_l . Yh_l) (cs x rE S); energies from its rows with weights |xb|
+        // B2t_l = Zc_l^T (Et_l . Yh_l) (cs x rE S), then the projected factors of the actual
+        // terms C_l[:, (k,j)] = sum_a B2t_l[:, (a,j)] Mt_l[a,k] for all cs directions (one GEMM
+        // per mode, batched over the S input columns j); the energy of mode l's column-
+        // normalised side matrix along direction i is sum_{(k,j)} w_l[k,j]^2 C_l[i,(k,j)]^2
         const long long RKt = (long long)CM * Kt;
         gemm_p(h->prec, st, cs, (int)Kt, n, LdT{w.Z, n, nC},
              LdKR{kr->Et, n, kr->bsEt, kr->Yh, n, (long long)n * h->KIN, kr->S}, 1.0, 0.0, w.C2, CM,
              RKt, d);
-        launch_outer_weights(st, kr->rE, h->ones, kr->S, kr->xb, w.wKt);
-        launch_row_energy(st, d, cs, (int)Kt, w.C2, CM, RKt, w.wKt, w.theta, CM);
+        for (int l = 0; l < d; ++l)
+            gemm_p(h->prec, st, cs, kr->Ra, kr->rE, LdColsJ{w.C2 + l * RKt, CM, kr->S},
+                 LdN{kr->Mt + l * kr->bsMt, kr->rE, 0}, 1.0, 0.0, w.C + l * RK, CM * kr->S, CM,
+                 kr->S);
+        launch_row_energy(st, d, cs, (int)K, w.C, CM, RK, w.wN, w.theta, CM, h->KMAX);
     } else {
         gemm_p(h->prec, st, cs, (int)K, n, LdT{w.Z, n, nC}, LdN{dn->U, dn->ld, dn->bs}, 1.0, 0.0, w.C, CM, RK,
              d);
@@ -504,15 +568,6 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
                          std::min(RM, cs), dims + D_R, w.scal + 8, dims + D_C1);
     launch_stage2_dims(st, d, dims);
     const int rz = std::min(RM, cs);
-    if (kr) {
-        // projected factors of the actual terms: C_l[:, (k,j)] = sum_a B2t_l[:, (a,j)] Mt_l[a,k]
-        // (first r_l rows), one GEMM per mode batched over the S input columns j
-        const long long RKt = (long long)CM * Kt;
-        for (int l = 0; l < d; ++l)
-            gemm_p(h->prec, st, cs, kr->Ra, kr->rE, LdColsJ{w.C2 + l * RKt, CM, kr->S},
-                 LdN{kr->Mt + l * kr->bsMt, kr->rE, 0}, 1.0, 0.0, w.C + l * RK, CM * kr->S, CM,
-                 kr->S, dims + D_R + l);
-    }
     CKL();
     // ---- core: B3[(a + r0 b), c] = sum_K w_K C0[a,K] C1[b,K] C2[c,K] ----------------------
     const int RR = RM * RM;
@@ -879,7 +934,9 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     // device tables
     const int N = n + 1;
     const int RAm = std::max(h->RA, h->RP);
-    size_t tcount = 3 * (size_t)n + 2 * N + h->RA + h->RP + h->RS + 2 * 3 * (size_t)n * RAm +
+    const bool pow2 = (N & (N - 1)) == 0 && N >= 2 && N <= 4096;
+    size_t tcount = 3 * (size_t)n + 2 * N + 4 * ((size_t)h->RA + h->RP + h->RS) + 2 * 3 * (size_t)n * RAm +
+                    (pow2 ? 2 * (size_t)N + 1 : 0) +
                     (varcoef ? 3 * (size_t)n * n : 0) +
                     3 * 3 * (size_t)n * n;
     if (cudaMalloc(&h->tables, tcount * sizeof(double)) != cudaSuccess) {
@@ -898,6 +955,14 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     h->GEP = p; p += 3 * (size_t)n * n;
     h->xiS = p; p += h->RS;
     h->GES = p; p += 3 * (size_t)n * n;
+    if (pow2) {                       // double2 table: 16-byte aligned start
+        p = h->tables + (((size_t)(p - h->tables) + 1) & ~(size_t)1);
+        h->twid = reinterpret_cast<double2*>(p);
+        p += 2 * (size_t)N;
+    }
+    h->xiAw = p; p += 3 * (size_t)h->RA;
+    h->xiPw = p; p += 3 * (size_t)h->RP;
+    h->xiSw = p; p += 3 * (size_t)h->RS;
     std::vector<double> tab(2 * N);
     const double sc = std::sqrt(2.0 / N);
     for (int m = 0; m < 2 * N; ++m) {
@@ -921,6 +986,21 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         if ((varcoef && cudaMemcpy(h->V, Vh.data(), sizeof(double) * Vh.size(), cudaMemcpyHostToDevice)) ||
             cudaMemcpy(h->lam, lam.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice) ||
             cudaMemcpy(h->sintab, tab.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice)) { rc = FC_ECUDA; break; }
+        if (pow2) {
+            // e^{-i pi k / N}: angle reduced to [0, pi/2] by the symmetries of sin and cos
+            std::vector<double> tw(2 * (size_t)N);
+            for (int k = 0; k < N; ++k) {
+                int q = k;
+                double c, sn_;
+                if (2 * q <= N) { c = std::cos(M_PI * q / N); sn_ = std::sin(M_PI * q / N); }
+                else { q = N - k; c = -std::cos(M_PI * q / N); sn_ = std::sin(M_PI * q / N); }
+                tw[2 * (size_t)k] = c;
+                tw[2 * (size_t)k + 1] = -sn_;
+            }
+            if (cudaMemcpy(h->twid, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice)) {
+                rc = FC_ECUDA; break;
+            }
+        }
         if (cudaMalloc(&dtau, sizeof(double) * RT) || cudaMalloc(&dw, sizeof(double) * RT) ||
             cudaMalloc(&dmode, sizeof(int) * RT)) { rc = FC_ECUDA; break; }
         cudaMemcpy(dtau, tau.data(), sizeof(double) * RT, cudaMemcpyHostToDevice);
@@ -931,13 +1011,17 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         launch_build_symbol(st, n, d, h->lam, n, dtau, dw, dmode, h->RA, h->EA, n, bsE, h->xiA);
         launch_build_symbol(st, n, d, h->lam, n, dtau + h->RA, dw + h->RA, dmode + h->RA, h->RP, h->EP,
                             n, bsP, h->xiP);
-        // mode Grams GE_l = E_l diag(xi^2) E_l^T  (weighted side-matrix Grams of the symbols)
-        const long long nn = (long long)n * n;
-        gemm(st, n, n, h->RA, LdSq{h->EA, n, bsE, h->xiA}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GEA, n, nn, d);
-        gemm(st, n, n, h->RP, LdSq{h->EP, n, bsP, h->xiP}, LdT{h->EP, n, bsP}, 1.0, 0.0, h->GEP, n, nn, d);
         // state symbol beta rho^-alpha = (beta^2 rho^-alpha part of the control symbol) / beta
         launch_copy_weights(st, h->RS, h->xiA, 1.0 / beta, h->xiS);
-        gemm(st, n, n, h->RS, LdSq{h->EA, n, bsE, h->xiS}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GES, n, nn, d);
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { rc = FC_ECUDA; break; }
+        if ((rc = symbol_proxy_weights(h)) != FC_OK) break;
+        // mode Grams GE_l = E_l diag(xw_l^2) E_l^T of the symbols' side matrices, with the
+        // per-mode dominating weights xw_l (symbol_proxy_weights)
+        const long long nn = (long long)n * n;
+        gemm(st, n, n, h->RA, LdSq{h->EA, n, bsE, h->xiAw, h->RA}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GEA, n, nn, d);
+        gemm(st, n, n, h->RP, LdSq{h->EP, n, bsP, h->xiPw, h->RP}, LdT{h->EP, n, bsP}, 1.0, 0.0, h->GEP, n, nn, d);
+        if (h->RS > 0)
+            gemm(st, n, n, h->RS, LdSq{h->EA, n, bsE, h->xiSw, h->RS}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GES, n, nn, d);
         if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { rc = FC_ECUDA; break; }
     } while (0);
     cudaFree(dtau); cudaFree(dw); cudaFree(dmode);
@@ -1101,11 +1185,11 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
              fc_solve_info* info, void* stream) {
     if (!h || !check_cp(h, rhs, false) || !check_cp(h, u, true)) return FC_EINVAL;
     if (!h->ws) return FC_EWORKSPACE;
-    fc_solve_opts opts{1e-8, 0.0, 100, 0, 0, 0};
+    fc_solve_opts opts{1e-8, 0.0, 100, 0, 0, 0, 0};
     if (o) opts = *o;
     if (!(opts.tol > 0.0)) opts.tol = 1e-8;
     if (opts.kmax <= 0) opts.kmax = 100;
-    if (opts.precision < 0 || opts.precision > 3) return FC_EINVAL;
+    if (opts.precision < 0 || opts.precision > 3 || opts.stall < 0) return FC_EINVAL;
     const double eps = (opts.eps > 0.0) ? opts.eps : h->eps;
     const int cap = std::min(h->CAP, (opts.max_rank > 0) ? opts.max_rank : h->CAP);
     if (u->cap < cap) { u->rank = cap; return FC_ERANK; }
@@ -1122,31 +1206,36 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     if (call.rc) return call.rc;
     auto& w = h->w;
     CP B = from_user(rhs);
-    CP &X = w.Xs, &R = w.Rs, &P = w.Ps, &Z = w.Zs, &S = w.Ss;
+    CP &X = w.Xs, &R = w.Rs, &P = w.Ps, &Z = w.Zs, &S = w.Ss, &Xb = w.Xb;
     int rc;
     double bn2;
     if ((rc = inner_impl(h, st, B, B, &bn2))) return rc;
     X.rank = 0;
+    Xb.rank = 0;
     double bscale = 1.0;
+    // the iterate returned: X, or with stall detection on an unconverged exit the iterate of
+    // the smallest residual (Xb)
+    bool use_best = false;
     auto finish = [&](int status) -> int {
+        const CP& Xr = use_best ? Xb : X;
         inf.status = status;
-        inf.rank_x = X.rank;
+        inf.rank_x = Xr.rank;
         inf.tucker_max = h->stat_rmax;
         inf.basis_max = h->stat_bmax;
         inf.tucker_mean = h->stat_rcount ? (double)h->stat_rsum / h->stat_rcount : 0.0;
         // X to the caller's u (spectral-resident: transformed back from the eigenbasis)
-        if (h->spectral && X.rank > 0) {
-            const double* xin[3] = {X.U[0], X.U[1], X.U[2]};
+        if (h->spectral && Xr.rank > 0) {
+            const double* xin[3] = {Xr.U[0], Xr.U[1], Xr.U[2]};
             double* uo[3] = {u->U[0], u->U[1], u->U[2]};
-            eig_transform_cols(h, st, X.rank, xin, X.ld, uo, u->ld, false);
+            eig_transform_cols(h, st, Xr.rank, xin, Xr.ld, uo, u->ld, false);
         } else {
             for (int l = 0; l < h->d; ++l)
-                if (X.rank > 0)
-                    CK(cudaMemcpy2DAsync(u->U[l], sizeof(double) * u->ld, X.U[l], sizeof(double) * X.ld,
-                                         sizeof(double) * h->n, X.rank, cudaMemcpyDeviceToDevice, st));
+                if (Xr.rank > 0)
+                    CK(cudaMemcpy2DAsync(u->U[l], sizeof(double) * u->ld, Xr.U[l], sizeof(double) * Xr.ld,
+                                         sizeof(double) * h->n, Xr.rank, cudaMemcpyDeviceToDevice, st));
         }
-        if (X.rank > 0) launch_copy_weights(st, X.rank, X.xi, bscale, u->xi);   // undo 1/||B||
-        u->rank = X.rank;
+        if (Xr.rank > 0) launch_copy_weights(st, Xr.rank, Xr.xi, bscale, u->xi);   // undo 1/||B||
+        u->rank = Xr.rank;
         if (int rf = flag_to_host(h, st)) return rf;
         CK(cudaStreamSynchronize(st));
         if (status == FC_OK && tc_status(h)) status = FC_ETIMEOUT;
@@ -1192,6 +1281,10 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     P.rank = Z.rank;
     double rz;
     if ((rc = inner_impl(h, st, R, Z, &rz))) return rc;
+    // stall detection (opts.stall > 0): the run ends once `stall` iterations in a row have not
+    // brought the recursive residual 10% below the last value that did
+    double best = INFINITY, anchor = INFINITY;
+    int since = 0;
     for (int k = 0; k < opts.kmax; ++k) {
         if ((rc = kr_trunc(h, st, P, 0, eps, cap, S))) return rc;        // S = trunc(fun(P))
         track(S);
@@ -1216,6 +1309,18 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         inf.relres = rel;
         if (!std::isfinite(rel)) return finish(FC_ENAN);
         if (rel <= opts.tol) return finish(FC_OK);
+        if (opts.stall > 0) {
+            if (rel < best) {                                   // keep the best iterate
+                best = rel;
+                for (int l = 0; l < h->d; ++l)
+                    CK(cudaMemcpyAsync(Xb.U[l], X.U[l], sizeof(double) * h->n * X.rank,
+                                       cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(Xb.xi, X.xi, sizeof(double) * X.rank, cudaMemcpyDeviceToDevice, st));
+                Xb.rank = X.rank;
+            }
+            if (rel <= 0.9 * anchor) { anchor = rel; since = 0; }
+            else if (++since >= opts.stall) { use_best = true; inf.relres = best; return finish(FC_ENOCONV); }
+        }
         if ((rc = kr_trunc(h, st, R, 1, eps, cap, Z))) return rc;          // Z = trunc(precond(R))
         track(Z);
         double rzn;
@@ -1225,6 +1330,7 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
         track(P);
         rz = rzn;
     }
+    if (opts.stall > 0 && Xb.rank > 0) { use_best = true; inf.relres = best; }
     return finish(FC_ENOCONV);
 }
 
@@ -1326,6 +1432,26 @@ int fc_full_solve(fc_handle h, const double* dev_rhs, double* dev_u, double* dev
     if (!h || !dev_rhs || !dev_u || !dev_tmp) return FC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const int n = h->n;
+    if (h->twid && !h->V) {
+        // fast sine transforms: forward passes over axes 0 .. d-2, then the last axis forward,
+        // divided by g and back in one pass, then the inverse passes (F = F^-1)
+        const SymbolSpec& g = h->spec;
+        const int d = h->d;
+        launch_dst_pass(st, dev_rhs, dev_u, d, 0, n, h->twid, false, h->lam, n, 0, 0, 0, 0, 0);
+        if (d == 2) {
+            launch_dst_pass(st, dev_u, dev_u, d, 1, n, h->twid, true, h->lam, n, g.a, g.sn, g.b,
+                            g.sp, g.c);
+        } else {
+            launch_dst_pass(st, dev_u, dev_u, d, 1, n, h->twid, false, h->lam, n, 0, 0, 0, 0, 0);
+            launch_dst_pass(st, dev_u, dev_u, d, 2, n, h->twid, true, h->lam, n, g.a, g.sn, g.b,
+                            g.sp, g.c);
+            launch_dst_pass(st, dev_u, dev_u, d, 1, n, h->twid, false, h->lam, n, 0, 0, 0, 0, 0);
+        }
+        launch_dst_pass(st, dev_u, dev_u, d, 0, n, h->twid, false, h->lam, n, 0, 0, 0, 0, 0);
+        CKL();
+        CK(cudaStreamSynchronize(st));
+        return FC_OK;
+    }
     LdSine F{h->sintab, 2 * (n + 1)};
     const long long nn = (long long)n * n;
     // y = (T_1 x .. x T_d) x  by d axis passes: T_l the DST-I (symmetric), or for per-mode

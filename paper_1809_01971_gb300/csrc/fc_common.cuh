@@ -11,6 +11,8 @@ namespace fc {
 
 // Count of kernels launched by this library in this process (fc_launch_count).
 void note_launch();
+// Record a CUDA error's text for fc_last_cuda_error (calling thread) and return FC_ECUDA.
+int record_cuda_error(cudaError_t e);
 
 // Kernel-class timing for instrumentation (fc_prof_*): while a class is enabled, each of
 // its launches is bracketed by a pair of CUDA events recorded on the launching stream.
@@ -75,9 +77,26 @@ struct LdScaledN {
 
 
 // ---- further operand loaders used by the truncation --------------------------------------
-struct LdSq {     // w_k^2 * X[i, k]
-    const double* p; int ld; long long bs; const double* w;
-    FC_DEV double operator()(int i, int k, int b) const { return w[k] * w[k] * p[b * bs + i + (long long)k * ld]; }
+struct LdSq {     // w_k^2 * X[i, k]  (w of batch item b at w + b * bsw)
+    const double* p; int ld; long long bs; const double* w; long long bsw = 0;
+    FC_DEV double operator()(int i, int k, int b) const {
+        const double wk = w[b * bsw + k];
+        return wk * wk * p[b * bs + i + (long long)k * ld];
+    }
+};
+struct LdSqN {    // X[i, k]^2
+    const double* p; int ld; long long bs;
+    FC_DEV double operator()(int i, int k, int b) const {
+        const double v = p[b * bs + i + (long long)k * ld];
+        return v * v;
+    }
+};
+struct LdSqT {    // X[k, i]^2  (op = transpose)
+    const double* p; int ld; long long bs;
+    FC_DEV double operator()(int i, int k, int b) const {
+        const double v = p[b * bs + k + (long long)i * ld];
+        return v * v;
+    }
 };
 struct LdAbsN {   // |w_k| * X[i, k]
     const double* p; int ld; long long bs; const double* w;

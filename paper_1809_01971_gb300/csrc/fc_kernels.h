@@ -38,6 +38,17 @@ void launch_select_terms(cudaStream_t st, const double* mu, int ldmu, const int*
                          int maxq, int* q_out, double* sigma, int* tslice, int* tidx,
                          double* dropped);
 
+// ---- k_fft.cu ------------------------------------------------------------------------
+// One pass of the full-format solve over an n^d column-major array (N = n + 1 a power of two,
+// N <= 4096): the orthonormal DST-I of every line of `axis` (in may equal out); with scale,
+// the line is transformed, divided by g(rho) = ga rho^-sn + gb rho^sp + gc and transformed
+// back (axis = d - 1).  tw[k] = e^{-i pi k / N}, k < N.
+void launch_dst_pass(cudaStream_t st, const double* in, double* out, int d, int axis, int n,
+                     const double2* tw, bool scale, const double* lam, int lstride, double ga,
+                     double sn, double gb, double sp, double gc);
+cudaError_t set_fft_attributes(int N);
+size_t fft_smem_bytes(int N, bool scale);
+
 // ---- k_tensor.cu ---------------------------------------------------------------------
 struct Piece { const double* xi; const double* U[3]; int ld; int K; double scale; };
 
@@ -76,25 +87,29 @@ void launch_sumsq(cudaStream_t st, int K, const double* w, double* out, int nout
 // out[l] = scale * sum_{e < count} p[l*stride + e]^2
 void launch_block_energy(cudaStream_t st, int d, long long count, const double* p,
                          long long stride, double scale, double* out);
-// rho[l*ldrho + i] = sum_{k < K} w_k^2 B[l*bs + i + k*ld]^2, i < rows
+// rho[l*ldrho + i] = sum_{k < K} w[l*bsw + k]^2 B[l*bs + i + k*ld]^2, i < rows
 void launch_row_energy(cudaStream_t st, int d, int rows, int K, const double* B, int ld,
-                       long long bs, const double* w, double* rho, int ldrho);
+                       long long bs, const double* w, double* rho, int ldrho, long long bsw = 0);
+// w[l*bsw + k*S + j] = |xa_k xb_j| prod_{m != l} sqrt(Nu[m*bsnu + k + j*ldnu]) (the column-
+// normalised weights of a Khatri-Rao tensor seen from mode l)
+void launch_kr_norm_weights(cudaStream_t st, int d, int Ra, int S, const double* xa,
+                            const double* xb, const double* Nu, int ldnu, long long bsnu,
+                            double* w, long long bsw);
 // mus[s*ldmu + i] = ||S_s y_{s,i}||^2 for slices s < dims[D_R3], i < dims[D_R+1]
 void launch_slice_energy(cudaStream_t st, int smax, int rmax, const int* dims, const double* S,
                          long long ldS, const double* V, int ldv, long long bsV, double* mus,
                          int ldmu);
-// ||w_a||^2 * ||w_b||^2 (KR weight norm); out[0]
-void launch_kr_wnorm(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,
-                     double* out);
 // stage-2 gather of the canonical terms into X_l (rmax x q, ld rmax) of each mode
 void launch_gather_terms(cudaStream_t st, int d, int rmax, const int* dims_r, const int* q,
                          int qmax, const double* sigma, const int* tslice, const int* tidx,
                          const double* core, int ldcore, const double* W3, int ldw3,
                          const double* Vs, int ldvs, long long bsVs, double* X, int ldx,
                          long long bsX);
-// out[0] = sum_{k<Rx, j<Ry} xi_k eta_j prod_l M_l[k,j]
+// out[0] = sum_{k<Rx, j<Ry} xi_k eta_j prod_l M_l[k,j]  (square: (xi_k eta_j)^2 in place of
+// xi_k eta_j)
 void launch_inner_reduce(cudaStream_t st, int d, int Rx, int Ry, const double* xi,
-                         const double* eta, const double* M, int ldm, long long bsM, double* out);
+                         const double* eta, const double* M, int ldm, long long bsM, double* out,
+                         bool square = false);
 void launch_to_full(cudaStream_t st, int d, int n, int R, const double* xi, const double* U0,
                     const double* U1, const double* U2, int ld, double* dense);
 // u_hat[i] /= g(rho_i), g = ga rho^-sn + gb rho^sp + gc, rho_i = sum_l lam[l*lstride + i_l]

@@ -314,14 +314,15 @@ void launch_block_energy(cudaStream_t st, int d, long long count, const double* 
 
 // one CTA per (row i, mode l): sum over the K columns of a row of a column-major matrix
 __global__ void row_energy_kernel(int K, const double* B, int ld, long long bs, const double* w,
-                                  double* rho, int ldrho)
+                                  long long bsw, double* rho, int ldrho)
 {
     __shared__ double red[32];
     const int i = blockIdx.x, l = blockIdx.y;
     const double* row = B + l * bs + i;
+    const double* wl = w + l * bsw;
     double s = 0.0;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double v = w[k] * row[(long long)k * ld];
+        double v = wl[k] * row[(long long)k * ld];
         s += v * v;
     }
     s = block_sum(s, red);
@@ -329,10 +330,40 @@ __global__ void row_energy_kernel(int K, const double* B, int ld, long long bs, 
 }
 
 void launch_row_energy(cudaStream_t st, int d, int rows, int K, const double* B, int ld,
-                       long long bs, const double* w, double* rho, int ldrho)
+                       long long bs, const double* w, double* rho, int ldrho, long long bsw)
 {
     if (rows <= 0) return;
-    note_launch(); row_energy_kernel<<<dim3(rows, d), 256, 0, st>>>(K, B, ld, bs, w, rho, ldrho);
+    note_launch();
+    row_energy_kernel<<<dim3(rows, d), 256, 0, st>>>(K, B, ld, bs, w, bsw, rho, ldrho);
+}
+
+// Column-normalised weights of a Khatri-Rao tensor, seen from mode l: the term (k, j) with
+// factors e_mk . y_mj has the normalised weight |xa_k xb_j| prod_m nu_m(k, j); its unit mode-l
+// column is (e_lk . y_lj) / nu_l, so in mode l's side matrix the column e_lk . y_lj carries
+// w_l[k S + j] = |xa_k xb_j| prod_{m != l} nu_m(k, j),  nu_m^2 = Nu[m bsnu + k + j ldnu].
+__global__ void kr_norm_weights_kernel(int d, int Ra, int S, const double* xa, const double* xb,
+                                       const double* Nu, int ldnu, long long bsnu, double* w,
+                                       long long bsw)
+{
+    const int l = blockIdx.y;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ra * S; e += gridDim.x * blockDim.x) {
+        const int k = e / S, j = e - k * S;
+        double v = fabs(xa[k] * xb[j]);
+        for (int m = 0; m < d; ++m)
+            if (m != l) v *= sqrt(fmax(Nu[m * bsnu + k + (long long)j * ldnu], 0.0));
+        w[l * bsw + e] = v;
+    }
+}
+
+void launch_kr_norm_weights(cudaStream_t st, int d, int Ra, int S, const double* xa,
+                            const double* xb, const double* Nu, int ldnu, long long bsnu,
+                            double* w, long long bsw)
+{
+    const int tot = Ra * S;
+    if (tot <= 0) return;
+    note_launch();
+    kr_norm_weights_kernel<<<dim3(std::min((tot + 255) / 256, 1024), d), 256, 0, st>>>(
+        d, Ra, S, xa, xb, Nu, ldnu, bsnu, w, bsw);
 }
 
 // mus[s*ldmu + i] = ||S_s y_i||^2, S_s compact r0 x r1 at S + s*ldS (element (a,b) at a + r0 b),
@@ -365,23 +396,6 @@ void launch_slice_energy(cudaStream_t st, int smax, int rmax, const int* dims, c
 {
     if (smax <= 0) return;
     note_launch(); slice_energy_kernel<<<smax, 256, 0, st>>>(rmax, dims, S, ldS, V, ldv, bsV, mus, ldmu);
-}
-
-__global__ void kr_wnorm_kernel(int Ra, const double* xa, int S, const double* xb, double* out)
-{
-    __shared__ double red[32];
-    double a = 0.0, b = 0.0;
-    for (int k = threadIdx.x; k < Ra; k += blockDim.x) a += xa[k] * xa[k];
-    for (int k = threadIdx.x; k < S; k += blockDim.x) b += xb[k] * xb[k];
-    a = block_sum(a, red);
-    b = block_sum(b, red);
-    if (threadIdx.x == 0) out[0] = a * b;
-}
-
-void launch_kr_wnorm(cudaStream_t st, int Ra, const double* xa, int S, const double* xb,
-                     double* out)
-{
-    note_launch(); kr_wnorm_kernel<<<1, 256, 0, st>>>(Ra, xa, S, xb, out);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -429,13 +443,15 @@ void launch_gather_terms(cudaStream_t st, int d, int rmax, const int* dims_r, co
 
 // <X, Y> = sum_{k,j} xi_k eta_j prod_l M_l[k, j]  (M_l = U_l^T V_l)
 __global__ void inner_reduce_kernel(int d, int Rx, int Ry, const double* xi, const double* eta,
-                                    const double* M, int ldm, long long bsM, double* out)
+                                    const double* M, int ldm, long long bsM, double* out,
+                                    int square)
 {
     __shared__ double red[32];
     double s = 0.0;
     for (int e = threadIdx.x; e < Rx * Ry; e += blockDim.x) {
         int k = e % Rx, j = e / Rx;
         double p = xi[k] * eta[j];
+        if (square) p *= p;
         for (int l = 0; l < d; ++l) p *= M[l * bsM + k + (long long)j * ldm];
         s += p;
     }
@@ -444,9 +460,11 @@ __global__ void inner_reduce_kernel(int d, int Rx, int Ry, const double* xi, con
 }
 
 void launch_inner_reduce(cudaStream_t st, int d, int Rx, int Ry, const double* xi,
-                         const double* eta, const double* M, int ldm, long long bsM, double* out)
+                         const double* eta, const double* M, int ldm, long long bsM, double* out,
+                         bool square)
 {
-    note_launch(); inner_reduce_kernel<<<1, 1024, 0, st>>>(d, Rx, Ry, xi, eta, M, ldm, bsM, out);
+    note_launch();
+    inner_reduce_kernel<<<1, 1024, 0, st>>>(d, Rx, Ry, xi, eta, M, ldm, bsM, out, square ? 1 : 0);
 }
 
 // full expansion, column-major with i_1 fastest

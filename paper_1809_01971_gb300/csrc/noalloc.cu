@@ -25,11 +25,15 @@ double* g_scratch_ptr[kMaxDev] = {nullptr};
 // Device address of the scratch array on the current device (looked up once per device).
 int scratch_for_current_device(double** out) {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return FC_ECUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fc::record_cuda_error(e);
+    if (dev < 0 || dev >= kMaxDev) return FC_EINVAL;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_inner_scratch) != cudaSuccess || !p) return FC_ECUDA;
+        e = cudaGetSymbolAddress(&p, g_inner_scratch);
+        if (e != cudaSuccess) return fc::record_cuda_error(e);
+        if (!p) return FC_ECUDA;
         g_scratch_ptr[dev] = static_cast<double*>(p);
     }
     *out = g_scratch_ptr[dev];
@@ -49,8 +53,8 @@ extern "C" int fc_inner_static(const fc_cp* x, const fc_cp* y, double* dev_out, 
     if (x->rank > FC_STATIC_MAX_RANK || y->rank > FC_STATIC_MAX_RANK) return FC_ERANK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (x->rank == 0 || y->rank == 0) {
-        if (cudaMemsetAsync(dev_out, 0, sizeof(double), st) != cudaSuccess) return FC_ECUDA;
-        return FC_OK;
+        cudaError_t e = cudaMemsetAsync(dev_out, 0, sizeof(double), st);
+        return e == cudaSuccess ? FC_OK : fc::record_cuda_error(e);
     }
     double* M = nullptr;
     int rc = scratch_for_current_device(&M);
@@ -63,5 +67,6 @@ extern "C" int fc_inner_static(const fc_cp* x, const fc_cp* y, double* dev_out, 
         fc::gemm(st, Rx, Ry, n, fc::LdT{x->U[l], x->ld, 0}, fc::LdN{y->U[l], y->ld, 0}, 1.0, 0.0,
                  M + l * mm, Rx);
     fc::launch_inner_reduce(st, d, Rx, Ry, x->xi, y->xi, M, Rx, mm, dev_out);
-    return cudaGetLastError() == cudaSuccess ? FC_OK : FC_ECUDA;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FC_OK : fc::record_cuda_error(e);
 }

@@ -58,7 +58,8 @@ class fc_setup_info(C.Structure):
 
 class fc_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("eps", C.c_double), ("kmax", C.c_int),
-                ("max_rank", C.c_int), ("spectral", C.c_int), ("precision", C.c_int)]
+                ("max_rank", C.c_int), ("spectral", C.c_int), ("precision", C.c_int),
+                ("stall", C.c_int)]
 
 
 class fc_solve_info(C.Structure):
@@ -350,13 +351,15 @@ def _form(precision):
 
 
 def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0, stream=None,
-             raise_on_fail: bool = True, spectral: bool = False, precision=None) -> fc_solve_info:
+             raise_on_fail: bool = True, spectral: bool = False, precision=None,
+             stall: int = 0) -> fc_solve_info:
     """Algorithm 1; spectral=True keeps every iterate in the DST-I eigenbasis (one transform
     at entry and exit instead of two per mat-vec: the same result).  precision: None for the
     handle's contraction form, else 0 FP64 / 1 double-float / 2 tensor-core digits for this
-    solve."""
+    solve.  stall > 0: stop after that many iterations without a 10% residual decrease and
+    return the best iterate (fc_solve_opts.stall)."""
     o = fc_solve_opts(float(tol), float(eps), int(kmax), int(max_rank), 1 if spectral else 0,
-                      _form(precision))
+                      _form(precision), int(stall))
     info = fc_solve_info()
     cr, cu = rhs.desc(), u.desc()
     rc = lib().fc_solve(h.ptr, C.byref(cr), C.byref(cu), C.byref(o), C.byref(info), _stream(stream))
@@ -368,7 +371,7 @@ def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
 
 def fc_solve_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
                      raise_on_fail: bool = True, spectral: bool = False, precision=None,
-                     stream=None):
+                     stream=None, stall: int = 0):
     """Independent solves run concurrently (a pool of up to 16 host threads, each on a worker
     stream of the library that starts after the work queued on ``stream`` and joins it).
     tol / eps / kmax / max_rank / precision are scalars or per-problem sequences."""
@@ -382,7 +385,8 @@ def fc_solve_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
     R = (fc_cp * count)(*[x.desc() for x in rhs])
     Uc = (fc_cp * count)(*[x.desc() for x in us])
     O = (fc_solve_opts * count)(*[fc_solve_opts(float(tols[i]), float(epss[i]), int(kms[i]),
-                                                int(mrs[i]), 1 if spectral else 0, _form(prs[i]))
+                                                int(mrs[i]), 1 if spectral else 0, _form(prs[i]),
+                                                int(stall))
                                   for i in range(count)])
     infos = (fc_solve_info * count)()
     rc = lib().fc_solve_batched(count, H, R, Uc, O, infos, _stream(stream))
@@ -416,8 +420,12 @@ def fc_inner_static(x: CP, y: CP, out: torch.Tensor, stream=None) -> torch.Tenso
     """<x, y> into the device scalar ``out`` without a handle or any allocation."""
     if out.dtype != torch.float64 or not out.is_cuda:
         raise ValueError("out must be a CUDA float64 tensor")
-    _check("fc_inner_static", lib().fc_inner_static(C.byref(x.desc()), C.byref(y.desc()),
-                                                    C.c_void_p(out.data_ptr()), _stream(stream)))
+    if x.xi.device != out.device or y.xi.device != out.device:
+        raise ValueError("x, y and out must be on the same CUDA device")
+    with torch.cuda.device(out.device):
+        _check("fc_inner_static", lib().fc_inner_static(C.byref(x.desc()), C.byref(y.desc()),
+                                                        C.c_void_p(out.data_ptr()),
+                                                        _stream(stream)))
     return out
 
 

@@ -50,10 +50,23 @@ def test_clock_record_without_samples_is_none():
     assert s.stop() is None
 
 
-def test_workload_is_the_six_3d_problems():
-    probs = bench.problems(6)
-    assert [(p.n, p.d) for p in probs] == [(255, 3)] * 6
-    assert sorted({p.alpha for p in probs}) == [0.25, 0.5, 0.75]
-    assert sorted({p.gamma for p in probs}) == [1e-3, 1e-1]
-    assert len({(p.alpha, p.gamma) for p in probs}) == 6
-    assert all(p.beta == 1.0 for p in probs)
+def test_workload_is_the_mixed_batch():
+    """The batching form's 512 problems: every grid class, alpha in [0.1, 0.9], gamma in
+    [1e-4, 1], rank 1-8 Gaussian right-hand sides, the 1e-6 settings."""
+    probs = bench.problems(512)
+    assert len(probs) == 512 and all(p.d == 3 and p.beta == 1.0 for p in probs)
+    assert {p.n for p in probs} == {127, 255, 511, 1023, 2047}
+    assert all(0.1 <= p.alpha <= 0.9 and 1e-4 <= p.gamma <= 1.0 for p in probs)
+    assert all(1 <= len(p.rhs()[0]) <= 8 for p in probs)
+    assert all((p.tol, p.eps, p.max_rank, p.max_tucker) == (1e-7, 1e-8, 256, 56) for p in probs)
+    ref = bench.reference_problem(probs)
+    assert ref.n == 127 and len(ref.rhs()[0]) == min(len(p.rhs()[0]) for p in probs if p.n == 127)
+
+
+def test_arguments_and_peaks():
+    a = bench.parse(["--steps", "4", "--warmup", "3", "--batch", "64"])
+    assert (a.steps, a.warmup, a.batch, a.impl) == (4, 3, 64, "ours")
+    assert "3d_mixed_batch_512problems" in bench.workload_name(512)
+    assert bench.workload_name(64).endswith("_step64")
+    pk = bench.alu_peaks(2070.0)
+    assert abs(pk["fp64_tflops"] - 1.25856) < 1e-9 and abs(pk["fp32_tflops"] - 80.54784) < 1e-6
