@@ -392,8 +392,12 @@ def main(argv=None):
     h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_in) * e2e_solved // BATCH_SET
     d2h = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_out) * e2e_solved // BATCH_SET
 
-    # roofline of the full-format solve kernel (fast sine transforms), timed here on its own
-    roofline = full_solve_roofline(fc, torch, dev, main_stream)
+    # rooflines: per kernel class, from CUDA events around each of its launches over the
+    # sample's solves run one after another on the main stream (isolated launches, outside the
+    # timed region); the dominant class by summed time is the headline roofline
+    classes = kernel_rooflines(fc, hs, Bs, Us, probs, sample, FORMS[best], main_stream)
+    dominant = max(classes, key=lambda r: r["event_ms"]) if classes else None
+    roofline_full = full_solve_roofline(fc, torch, dev, main_stream)
     if rank == 0:
         name, _, _, dtype, what = FORMS[best]
         forms = {FORMS[f][0]: survey[f] for f in sorted(survey)}
@@ -419,7 +423,9 @@ def main(argv=None):
                         "d2h_bytes_per_step": d2h // n_e2e},
                 "gpu_launches": int(launches),
                 "clocks": clocks,
-                "roofline": roofline,
+                "roofline": dominant,
+                "rooflines_by_kernel": classes,
+                "roofline_full_solve": roofline_full,
                 "cpu_baseline": None}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(probs)
@@ -427,6 +433,49 @@ def main(argv=None):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0 if err_best <= args.max_err else 3
+
+
+def kernel_rooflines(fc, hs, Bs, Us, probs, sample, form, stream):
+    """Achieved rate of the three kernel classes that carry the solve's work (the FP64 tiled
+    GEMM, the tensor-core digit GEMM, the graded eigen-solver) over the sample's solves, each
+    class instrumented in its own pass (fc_prof_enable: a CUDA event pair around every launch
+    of the class on its stream, algorithmic work counted on the device)."""
+    _, prec, spectral, _, _ = form
+    peaks = measured_peaks()
+    alu = alu_peaks()
+    specs = [
+        (fc.fc.PROF_F64, "gemm_kernel (FP64 tiled GEMM: Grams, bases, inner products, the "
+                         "contractions below 2^24 multiply-adds)", "alu", alu["fp64_tflops"],
+         "FP64 pipe, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+         "2 flop per multiply-add of the live tiles"),
+        (fc.fc.PROF_TC, "gemm_tc_kernel (FP64-accurate contractions as BF16 digit-pair MMAs on "
+                        "tcgen05, TMEM accumulators)", "tensor",
+         float(peaks.get("bf16_tflops_sustained", 1708.8)),
+         "measured BF16 dense, sustained (MEASURED_PEAKS.json)",
+         "BF16 MMA flops issued: 36 digit pairs x 2 x 128 x N_tile per K"),
+        (fc.fc.PROF_JACOBI, "gjacobi_kernel (graded eigen-solves of the RHOSVD: FP32 Jacobi "
+                            "sweeps, FP64 orthonormalisation; one CTA per matrix)", "alu",
+         alu["fp32_tflops"], "FP32 pipe, derived: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
+         "9 c^3 flop per c x c matrix (textbook count of a dense symmetric eigen-solve)"),
+    ]
+    out = []
+    for kclass, kernel, bound, peak, peak_kind, work_kind in specs:
+        fc.fc_prof_enable(kclass)
+        for i in sample:
+            fc.fc_solve(hs[i], Bs[i], Us[i], tol=probs[i].tol, eps=probs[i].eps,
+                        precision=prec, spectral=spectral, stall=STALL, stream=stream,
+                        raise_on_fail=False)
+        n_launch, ms, work = fc.fc_prof_read()
+        if n_launch == 0 or ms <= 0:
+            continue
+        achieved = work / (ms * 1e-3) / 1e12
+        out.append({"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_kind": peak_kind, "work": work_kind, "launches": n_launch,
+                    "event_ms": ms, "avg_launch_us": 1e3 * ms / n_launch,
+                    "timing": f"isolated launches over {len(sample)} sample solves run one "
+                              f"after another (CUDA events on the launching stream)"})
+    return out
 
 
 def full_solve_roofline(fc, torch, dev, stream, n=1023):

@@ -307,7 +307,8 @@ int fc_dgemm(int precision, int transA, int transB, int M, int N, int K, double 
  * events on its stream and accumulates the class's algorithmic work on the device.
  * kclass: 0 = off, 1 = the small eigen-solver (work = 9 c^3 flops per c x c matrix),
  * 2 = the tensor-core contraction (work = BF16 MMA flops issued: 36 digit-pair products per
- * multiply-add of the FP64 contraction, tiles padded to 128 x N).
+ * multiply-add of the FP64 contraction, tiles padded to 128 x N), 3 = the FP64 tiled GEMM
+ * (work = 2 flops per multiply-add of its live tiles).
  * fc_prof_read disables it, synchronises, and returns the launches, the summed event time of
  * those launches in ms, and the work (flops). */
 int fc_prof_enable(int kclass);

@@ -41,25 +41,30 @@ def main(argv=None) -> int:
     else:
         probs = [fi.config1() if args.problem == "2d" else fi.config2(int(args.problem))]
     stream = torch.cuda.current_stream()
+    # set-up of every problem first; the solves run inside the NVTX range "fc_solve" (a
+    # profiler can select them with it)
+    work = []
     for prob in probs:
         h = fc.fc_setup(prob.n, prob.d, prob.alpha, prob.beta, prob.gamma, prob.eps,
                         max_rank=prob.max_rank, max_tucker=prob.max_tucker,
                         precision=args.precision)
-        B = fc.CP.from_factors(*prob.rhs())
-        U = fc.CP(prob.d, prob.n, prob.max_rank)
+        work.append((prob, h, fc.CP.from_factors(*prob.rhs()), fc.CP(prob.d, prob.n, prob.max_rank)))
+    torch.cuda.synchronize()
+    for prob, h, B, U in work:
         for r in range(max(1, args.repeats)):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("fc_solve")
             e0.record(stream)
             info = fc.fc_solve(h, B, U, tol=prob.tol, eps=prob.eps, spectral=args.spectral,
                                stall=8 if args.batch else 0, raise_on_fail=False)
             e1.record(stream)
             e1.synchronize()
+            torch.cuda.nvtx.range_pop()
             print(f"{prob.label} precision={args.precision} solve {r}: status {info.status} "
                   f"iters {info.iters} relres {info.relres:.2e} rank {U.rank} "
                   f"max rank {info.max_rank_seen} truncations {info.trunc_calls} "
                   f"{e0.elapsed_time(e1):.2f} ms", flush=True)
-        h.destroy()
     return 0
 
 

@@ -123,10 +123,10 @@ struct fc_ctx {
     // device tables (owned)
     double* tables = nullptr;
     double *lam = nullptr, *sintab = nullptr;
-    double *xiA = nullptr, *EA = nullptr, *GEA = nullptr;   // symbol CP and mode Grams
-    double *xiP = nullptr, *EP = nullptr, *GEP = nullptr;   // preconditioner CP and Grams
+    double *xiA = nullptr, *EA = nullptr;   // symbol CP (weights, unit-column mode factors)
+    double *xiP = nullptr, *EP = nullptr;   // preconditioner CP
     // state symbol beta rho^-alpha: the first RS columns of EA with weights xiA / beta
-    double *xiS = nullptr, *GES = nullptr;
+    double *xiS = nullptr;
     // dominating column weights of the three symbols' Khatri-Rao side matrices, per mode
     // (mode stride R): xw_l[k] = |xi_k| prod_{m != l} max_i |E_m[i, k]| (see symbol_proxy_weights)
     double *xiAw = nullptr, *xiPw = nullptr, *xiSw = nullptr;
@@ -150,7 +150,7 @@ struct fc_ctx {
     size_t ws_bytes = 0;
     // workspace slices
     struct {
-        double *Y, *Y2, *Q, *tmp, *M, *Tm, *GY, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *wK, *C2, *wN;
+        double *Y, *Y2, *Q, *tmp, *M, *Tm, *GQ, *Tr, *theta, *Vr, *Z, *Zr, *C, *Cq, *wK, *C2, *wN;
         double *core, *G3, *ev3, *W3, *Srot, *SG, *mus, *Vs, *sigma, *X, *Yh, *Nu;
         double *scal, *Mi;
         int *dims, *tslice, *tidx;
@@ -180,7 +180,6 @@ size_t layout(fc_ctx* h, Arena& a) {
     w.tmp = a.d(3 * nC);
     w.M = a.d(3 * (size_t)CM * CM);
     w.Tm = a.d(3 * (size_t)CM * CM);
-    w.GY = a.d(3 * (size_t)n * n);
     w.GQ = a.d(3 * nC);
     w.Tr = a.d(3 * (size_t)CM * CM);
     w.theta = a.d(3 * (size_t)CM);
@@ -188,6 +187,7 @@ size_t layout(fc_ctx* h, Arena& a) {
     w.Z = a.d(3 * nC);
     w.Zr = a.d(3 * nC);
     w.C = a.d(3 * (size_t)std::max(RM, CM) * K);
+    w.Cq = a.d(3 * (size_t)CM * K);
     w.wK = a.d((size_t)K);
     w.C2 = a.d(3 * (size_t)CM * std::max<long long>(1, (long long)h->rEmax * h->KIN));
     w.wN = a.d(3 * (size_t)K);
@@ -252,11 +252,11 @@ constexpr double kCompressTol = 1e-14;
 // Dominating weights of a symbol's Khatri-Rao side matrices (cold path, host).  A mat-vec
 // output has the terms xa_k xb_j (x)_l (e_lk . y_lj) with unit e_lk, y_lj; its columns are not
 // unit vectors (nu_l(k, j) = ||e_lk . y_lj|| <= ||e_lk||_inf), so the column-normalised tensor
-// has the weights |xa_k xb_j| prod_l nu_l(k, j).  The stage-1 side matrix of mode l is taken with
+// has the weights |xa_k xb_j| prod_l nu_l(k, j).  The stage-1 sketch of mode l is taken with
 // the columns e_lk . y_lj and the weights |xa_k xb_j| prod_{m != l} ||e_mk||_inf, which dominate
-// the normalised weights column by column, so every energy it measures bounds the normalised
-// one, while the weights keep the Khatri-Rao product form (xa_k-part times xb_j) that the
-// structured sketch and the Hadamard Gram GE . GY need.
+// the normalised weights column by column, so the energy it leaves outside its basis bounds
+// the normalised one, while the weights keep the Khatri-Rao product form (xa_k-part times xb_j)
+// that the structured sketch and the compressed symbol factors need.
 int symbol_proxy_weights(fc_ctx* h) {
     const int n = h->n, d = h->d;
     const int Rs[3] = {h->RA, h->RP, h->RS};
@@ -380,7 +380,7 @@ void eig_transform_cols(fc_ctx* h, cudaStream_t st, int cols, const double* cons
 }
 
 struct KRIn {           // implicit Khatri-Rao tensor sum_{k,j} xa_k xb_j (x)_l E_l[:,k].Yh_l[:,j]
-    const double* xa; const double* E; int Ra; long long bsE; const double* GE;
+    const double* xa; const double* E; int Ra; long long bsE;
     const double* xb; const double* Yh; int S;
     // compressed symbol factors E_l ~ Et_l Mt_l (Et_l: n x rE, Mt_l: rE x Ra, mode strides
     // bsEt, bsMt); Et_l has the same Gram as E_l diag|xa|, so the Khatri-Rao tensor's side
@@ -506,13 +506,8 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     }
     // Rayleigh-Ritz matrix T = Q^T W W^T Q: its eigenvectors order the basis (largest
     // energy first); the energies themselves are taken from the projections below.
+    const long long RK = (long long)CM * K;
     if (kr) {
-        // GY = Yh diag(xb^2) Yh^T ;  T = Q^T (GE . GY) Q
-        const long long nn = (long long)n * n;
-        gemm(st, n, n, kr->S, LdSq{kr->Yh, n, (long long)n * h->KIN, kr->xb},
-             LdT{kr->Yh, n, (long long)n * h->KIN}, 1.0, 0.0, w.GY, n, nn, d);
-        gemm(st, n, cs, n, LdHad{kr->GE, w.GY, n, nn, nn}, LdN{Qb, n, nC}, 1.0, 0.0, w.GQ, n, nC, d);
-        gemm(st, cs, cs, n, LdT{Qb, n, nC}, LdN{w.GQ, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
         // budget scale: the norm of the column-normalised weights,
         // sum_{k,j} (xa_k xb_j)^2 prod_l nu_l(k,j)^2 with nu_l(k,j)^2 = ((E_l.E_l)^T (Yh_l.Yh_l))[k,j]
         gemm(st, kr->Ra, kr->S, n, LdSqT{kr->E, n, kr->bsE}, LdSqN{kr->Yh, n, (long long)n * h->KIN},
@@ -524,6 +519,20 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         launch_kr_norm_weights(st, d, kr->Ra, kr->S, kr->xa, kr->xb, w.Nu, kr->Ra,
                                (long long)std::max(h->RA, h->RP) * h->KIN, w.wN, h->KMAX);
         launch_outer_weights(st, kr->Ra, kr->xa, kr->S, kr->xb, w.wK);
+        // projections of every term onto the basis: B2t_l = Q_l^T (Et_l . Yh_l) (cs x rE S)
+        // through the compressed symbol factors, then Cq_l[:, (k,j)] = sum_a B2t_l[:, (a,j)]
+        // Mt_l[a,k] (one GEMM per mode, batched over the S input columns j)
+        const long long RKt = (long long)CM * Kt;
+        gemm_p(h->prec, st, cs, (int)Kt, n, LdT{Qb, n, nC},
+             LdKR{kr->Et, n, kr->bsEt, kr->Yh, n, (long long)n * h->KIN, kr->S}, 1.0, 0.0, w.C2, CM,
+             RKt, d);
+        for (int l = 0; l < d; ++l)
+            gemm_p(h->prec, st, cs, kr->Ra, kr->rE, LdColsJ{w.C2 + l * RKt, CM, kr->S},
+                 LdN{kr->Mt + l * kr->bsMt, kr->rE, 0}, 1.0, 0.0, w.Cq + l * RK, CM * kr->S, CM,
+                 kr->S);
+        // T_l = Cq_l diag(w_l^2) Cq_l^T with the column-normalised weights of mode l
+        gemm_p(h->prec, st, cs, cs, (int)K, LdSq{w.Cq, CM, RK, w.wN, h->KMAX}, LdT{w.Cq, CM, RK},
+               1.0, 0.0, w.Tr, CM, CC, d);
     } else {
         // Bq = Q^T W (cs x K) in w.C, T = Bq Bq^T
         double* Bq = w.C;
@@ -534,29 +543,20 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         launch_sumsq(st, (int)K, dn->w, w.scal + 4, 1);
     }
     CKL();
-    // the Khatri-Rao Rayleigh-Ritz matrix comes from the n x n Hadamard Gram (normwise
-    // accurate); the dense one from the projected rows (row-graded)
+    // both Rayleigh-Ritz matrices come from projected rows (row-graded)
     launch_gjacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC, false,
-                   kr ? 1e-15f : 1e-20f);
+                   1e-20f);
     // Zc_l = Q_l Vr_l (all cs Ritz directions, descending)
     gemm(st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
     // B2_l = Zc_l^T U_l (cs x K, unweighted): its first r_l rows are the projected factors C_l
     // of the core; rho_i = sum_K w_K^2 B2[i, K]^2 is the energy of W_l along Ritz direction i
-    const long long RK = (long long)CM * K;
     const double* wK = dn ? dn->w : w.wK;
     if (kr) {
-        // B2t_l = Zc_l^T (Et_l . Yh_l) (cs x rE S), then the projected factors of the actual
-        // terms C_l[:, (k,j)] = sum_a B2t_l[:, (a,j)] Mt_l[a,k] for all cs directions (one GEMM
-        // per mode, batched over the S input columns j); the energy of mode l's column-
-        // normalised side matrix along direction i is sum_{(k,j)} w_l[k,j]^2 C_l[i,(k,j)]^2
-        const long long RKt = (long long)CM * Kt;
-        gemm_p(h->prec, st, cs, (int)Kt, n, LdT{w.Z, n, nC},
-             LdKR{kr->Et, n, kr->bsEt, kr->Yh, n, (long long)n * h->KIN, kr->S}, 1.0, 0.0, w.C2, CM,
-             RKt, d);
-        for (int l = 0; l < d; ++l)
-            gemm_p(h->prec, st, cs, kr->Ra, kr->rE, LdColsJ{w.C2 + l * RKt, CM, kr->S},
-                 LdN{kr->Mt + l * kr->bsMt, kr->rE, 0}, 1.0, 0.0, w.C + l * RK, CM * kr->S, CM,
-                 kr->S);
+        // C_l = Vr_l^T Cq_l: the projections of the terms onto the Ritz directions; the energy
+        // of mode l's column-normalised side matrix along direction i is
+        // sum_{(k,j)} w_l[k,j]^2 C_l[i,(k,j)]^2
+        gemm_p(h->prec, st, cs, (int)K, cs, LdT{w.Vr, CM, CC}, LdN{w.Cq, CM, RK}, 1.0, 0.0, w.C,
+               CM, RK, d);
         launch_row_energy(st, d, cs, (int)K, w.C, CM, RK, w.wN, w.theta, CM, h->KMAX);
     } else {
         gemm_p(h->prec, st, cs, (int)K, n, LdT{w.Z, n, nC}, LdN{dn->U, dn->ld, dn->bs}, 1.0, 0.0, w.C, CM, RK,
@@ -654,11 +654,11 @@ int kr_from(fc_ctx* h, cudaStream_t st, const CP& x, int which, KRIn& kr) {
         eig_transform_cols(h, st, x.rank, in, x.ld, o, h->n, true);
     }
     if (which == 1) {
-        kr.xa = h->xiP; kr.E = h->EP; kr.Ra = h->RP; kr.bsE = (long long)h->n * h->RP; kr.GE = h->GEP;
+        kr.xa = h->xiP; kr.E = h->EP; kr.Ra = h->RP; kr.bsE = (long long)h->n * h->RP;
     } else if (which == 2) {
-        kr.xa = h->xiS; kr.E = h->EA; kr.Ra = h->RS; kr.bsE = (long long)h->n * h->RA; kr.GE = h->GES;
+        kr.xa = h->xiS; kr.E = h->EA; kr.Ra = h->RS; kr.bsE = (long long)h->n * h->RA;
     } else {
-        kr.xa = h->xiA; kr.E = h->EA; kr.Ra = h->RA; kr.bsE = (long long)h->n * h->RA; kr.GE = h->GEA;
+        kr.xa = h->xiA; kr.E = h->EA; kr.Ra = h->RA; kr.bsE = (long long)h->n * h->RA;
     }
     const int sidx = (which == 1) ? 1 : (which == 2 ? 2 : 0);
     kr.rE = h->rE[sidx];
@@ -787,7 +787,7 @@ int fc_dgemm(int precision, int transA, int transB, int M, int N, int K, double 
 }
 
 int fc_prof_enable(int kclass) {
-    if (kclass < 0 || kclass > KC_TC) return FC_EINVAL;
+    if (kclass < 0 || kclass > KC_F64) return FC_EINVAL;
     std::lock_guard<std::mutex> lock(g_prof_mu);
     if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError());
     g_prof_used = 0;
@@ -937,8 +937,7 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     const bool pow2 = (N & (N - 1)) == 0 && N >= 2 && N <= 4096;
     size_t tcount = 3 * (size_t)n + 2 * N + 4 * ((size_t)h->RA + h->RP + h->RS) + 2 * 3 * (size_t)n * RAm +
                     (pow2 ? 2 * (size_t)N + 1 : 0) +
-                    (varcoef ? 3 * (size_t)n * n : 0) +
-                    3 * 3 * (size_t)n * n;
+                    (varcoef ? 3 * (size_t)n * n : 0);
     if (cudaMalloc(&h->tables, tcount * sizeof(double)) != cudaSuccess) {
         delete h;
         return FC_ECUDA;
@@ -951,10 +950,8 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
     h->xiP = p; p += h->RP;
     h->EA = p; p += 3 * (size_t)n * RAm;
     h->EP = p; p += 3 * (size_t)n * RAm;
-    h->GEA = p; p += 3 * (size_t)n * n;
-    h->GEP = p; p += 3 * (size_t)n * n;
+
     h->xiS = p; p += h->RS;
-    h->GES = p; p += 3 * (size_t)n * n;
     if (pow2) {                       // double2 table: 16-byte aligned start
         p = h->tables + (((size_t)(p - h->tables) + 1) & ~(size_t)1);
         h->twid = reinterpret_cast<double2*>(p);
@@ -1015,14 +1012,6 @@ int fc_setup(int n, int d, double alpha, double beta, double gamma, double eps,
         launch_copy_weights(st, h->RS, h->xiA, 1.0 / beta, h->xiS);
         if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { rc = FC_ECUDA; break; }
         if ((rc = symbol_proxy_weights(h)) != FC_OK) break;
-        // mode Grams GE_l = E_l diag(xw_l^2) E_l^T of the symbols' side matrices, with the
-        // per-mode dominating weights xw_l (symbol_proxy_weights)
-        const long long nn = (long long)n * n;
-        gemm(st, n, n, h->RA, LdSq{h->EA, n, bsE, h->xiAw, h->RA}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GEA, n, nn, d);
-        gemm(st, n, n, h->RP, LdSq{h->EP, n, bsP, h->xiPw, h->RP}, LdT{h->EP, n, bsP}, 1.0, 0.0, h->GEP, n, nn, d);
-        if (h->RS > 0)
-            gemm(st, n, n, h->RS, LdSq{h->EA, n, bsE, h->xiSw, h->RS}, LdT{h->EA, n, bsE}, 1.0, 0.0, h->GES, n, nn, d);
-        if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { rc = FC_ECUDA; break; }
     } while (0);
     cudaFree(dtau); cudaFree(dw); cudaFree(dmode);
     if (rc == FC_OK) rc = compress_symbols(h);

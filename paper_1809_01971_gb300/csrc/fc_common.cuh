@@ -16,7 +16,7 @@ int record_cuda_error(cudaError_t e);
 
 // Kernel-class timing for instrumentation (fc_prof_*): while a class is enabled, each of
 // its launches is bracketed by a pair of CUDA events recorded on the launching stream.
-enum KernelClass { KC_NONE = 0, KC_JACOBI = 1, KC_TC = 2 };
+enum KernelClass { KC_NONE = 0, KC_JACOBI = 1, KC_TC = 2, KC_F64 = 3 };
 struct ProfMark { int slot = -1; };
 bool prof_active(int kclass);
 void prof_begin(cudaStream_t st, ProfMark& m);
@@ -102,12 +102,6 @@ struct LdAbsN {   // |w_k| * X[i, k]
     const double* p; int ld; long long bs; const double* w;
     FC_DEV double operator()(int i, int k, int b) const { return fabs(w[k]) * p[b * bs + i + (long long)k * ld]; }
 };
-struct LdHad {    // A[i, k] * B[i, k]  (n x n Hadamard product of two Grams)
-    const double* A; const double* B; int n; long long bsA, bsB;
-    FC_DEV double operator()(int i, int k, int b) const {
-        return A[b * bsA + i + (long long)k * n] * B[b * bsB + i + (long long)k * n];
-    }
-};
 // A[(a + r0 b), k] = w_k C0[a, k] C1[b, k], r0 read from device memory
 struct LdCore {
     const double* C0; const double* C1; const double* w; int ldc; const int* r0p;
@@ -164,7 +158,7 @@ template <int T, class LA, class LB>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
             LA A, LB B, double alpha, double beta, double* C, int ldc, long long bsC,
-            int batch, int splits, int kchunk)
+            int batch, int splits, int kchunk, unsigned long long* work)
 {
     constexpr int R = T / 16;                  // register block per thread
     constexpr int LOADS = T * GBK / 256;       // tile elements loaded per thread
@@ -227,6 +221,10 @@ gemm_kernel(int M, int N, int K, const int* dM, const int* dN, const int* dK,
             else *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
         }
     }
+    // instrumentation: 2 flop per multiply-add of the live tile and K range
+    if (work && threadIdx.x == 0 && kend > kbeg)
+        atomicAdd(work, 2ull * (unsigned long long)min(T, M - m0) * (unsigned long long)min(T, N - n0) *
+                            (unsigned long long)(kend - kbeg));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -380,6 +378,10 @@ inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, d
     }
     dim3 grid((M + T - 1) / T, (N + T - 1) / T, batch * splits);
     note_launch();
+    const bool prof = prec != GP_DF32 && prof_active(KC_F64);
+    unsigned long long* work = prof ? prof_work_counter() : nullptr;
+    ProfMark mark;
+    if (prof) prof_begin(st, mark);
     if (prec == GP_DF32) {
         if (T == 64)
             gemm_df_kernel<64, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta,
@@ -394,13 +396,14 @@ inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, d
     }
     if (T == 64)
         gemm_kernel<64, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
-                                                      ldc, bsC, batch, splits, kchunk);
+                                                      ldc, bsC, batch, splits, kchunk, work);
     else if (T == 32)
         gemm_kernel<32, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
-                                                      ldc, bsC, batch, splits, kchunk);
+                                                      ldc, bsC, batch, splits, kchunk, work);
     else
         gemm_kernel<16, LA, LB><<<grid, 256, 0, st>>>(M, N, K, dM, dN, dK, A, B, alpha, beta, C,
-                                                      ldc, bsC, batch, splits, kchunk);
+                                                      ldc, bsC, batch, splits, kchunk, work);
+    if (prof) prof_end(st, mark);
 }
 
 template <class LA, class LB>

@@ -472,6 +472,7 @@ def fc_dgemm(A: torch.Tensor, B: torch.Tensor, precision: int = 2, alpha: float 
 
 PROF_JACOBI = 1
 PROF_TC = 2
+PROF_F64 = 3
 
 
 def fc_prof_enable(kclass: int) -> None:
