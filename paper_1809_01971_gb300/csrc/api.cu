@@ -91,6 +91,10 @@ struct CP {
     long long bs() const { return (long long)ld * cap; }
 };
 
+// Fraction of a truncation budget below which the eigen-solves leave an off-diagonal entry
+// unrotated (launch_gjacobi's absolute floor).
+constexpr double kEnergyFloor = 0.01;
+
 // Linear bump allocator over the caller's workspace (256-byte aligned slices).
 struct Arena {
     char* base = nullptr;
@@ -543,9 +547,12 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         launch_sumsq(st, (int)K, dn->w, w.scal + 4, 1);
     }
     CKL();
-    // both Rayleigh-Ritz matrices come from projected rows (row-graded)
+    // both Rayleigh-Ritz matrices come from projected rows (row-graded).  The energies that
+    // decide the ranks are measured by projection for whatever basis the solver returns, so
+    // off-diagonal entries far below the stage-1 budget (eps ||w||)^2 / (2d) need no rotation:
+    // they are skipped below 1 % of it
     launch_gjacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC, false,
-                   1e-20f);
+                   1e-20f, w.scal + 4, kEnergyFloor * eps * eps / (2.0 * d));
     // Zc_l = Q_l Vr_l (all cs Ritz directions, descending)
     gemm(st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
     // B2_l = Zc_l^T U_l (cs x K, unweighted): its first r_l rows are the projected factors C_l
@@ -597,13 +604,16 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     // mode-3 rotation: G3 = B3^T B3, W3 = eigvecs, Srot = B3 W3
     gemm(st, RM, RM, RR, LdT{w.core, RR, 0}, LdN{w.core, RR, 0}, 1.0, 0.0, w.G3, RM, 0, 1,
          dims + D_R3, dims + D_R3, dims + D_R12);
-    launch_gjacobi(st, 1, w.G3, RM, 0, dims + D_R3, 0, RM, w.ev3, 0, w.W3, RM, 0, false);
+    // stage-2 Grams: the same floor against the stage-2 budget (eps ||core||)^2 / 2
+    launch_gjacobi(st, 1, w.G3, RM, 0, dims + D_R3, 0, RM, w.ev3, 0, w.W3, RM, 0, false, 1e-20f,
+                   w.scal + 12, kEnergyFloor * eps * eps / 2.0);
     gemm(st, RR, RM, RM, LdN{w.core, RR, 0}, LdN{w.W3, RM, 0}, 1.0, 0.0, w.Srot, RR, 0, 1,
          dims + D_R12, dims + D_R3, dims + D_R3);
     // slice Grams SG[s] = S_s^T S_s  (S_s = r0 x r1, compact column s of Srot)
     gemm(st, RM, RM, RM, LdSlT{w.Srot, RR, dims + D_R}, LdSl{w.Srot, RR, dims + D_R}, 1.0, 0.0,
          w.SG, RM, RR, (d == 3) ? RM : 1, dims + D_R + 1, dims + D_R + 1, dims + D_R);
-    launch_gjacobi(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR, false);
+    launch_gjacobi(st, (d == 3) ? RM : 1, w.SG, RM, RR, dims + D_R + 1, 0, RM, w.mus, RM, w.Vs, RM, RR, false,
+                   1e-20f, w.scal + 12, kEnergyFloor * eps * eps / 2.0);
     // candidate term energies ||S_s y_i||^2 taken directly (not the Gram eigenvalues)
     launch_slice_energy(st, (d == 3) ? RM : 1, RM, dims, w.Srot, RR, w.Vs, RM, RR, w.mus, RM);
     CKL();

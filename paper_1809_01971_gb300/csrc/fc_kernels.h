@@ -17,10 +17,12 @@ void launch_symeig(cudaStream_t st, int batch, const double* A, int lda, long lo
 size_t symeig_smem();
 // Graded variant (FP32 Jacobi + FP64 orthonormalisation), same contract; eigenvalues are FP64
 // Rayleigh quotients if rq, else the FP32 Jacobi values.  floorRel: off-diagonal entries below
-// floorRel * max diagonal are treated as zero (the rounding level of the Gram's formation).
+// floorRel * max diagonal are treated as zero (the rounding level of the Gram's formation);
+// with floorAbs (device pointer) also those below floorFrac * (*floorAbs) in absolute terms.
 void launch_gjacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
                     const int* dims, int dstride, int cmax, double* ev, long long bsE,
-                    double* V, int ldv, long long bsV, bool rq, float floorRel = 1e-20f);
+                    double* V, int ldv, long long bsV, bool rq, float floorRel = 1e-20f,
+                    const double* floorAbs = nullptr, double floorFrac = 0.0);
 size_t gjacobi_smem();
 cudaError_t set_symeig_attributes();
 // Opt the large-shared-memory kernels in to their dynamic shared memory (per device).

@@ -353,7 +353,8 @@ constexpr int kGjThreads = 1024;
 __global__ void __launch_bounds__(kGjThreads, 1)
 gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* __restrict__ dims,
                int dstride, int cmax, double* __restrict__ ev, long long bsE,
-               double* __restrict__ V, int ldv, long long bsV, int rq, float floorRel, int prof)
+               double* __restrict__ V, int ldv, long long bsV, int rq, float floorRel, int prof,
+               const double* __restrict__ floorAbs, double floorFrac)
 {
     extern __shared__ double sm[];
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -408,6 +409,12 @@ gjacobi_kernel(const double* __restrict__ A, int lda, long long bsA, const int* 
         return;
     }
     const double sc = 1.0 / dmax;
+    // absolute floor (energy units): off-diagonal entries below floorFrac * (*floorAbs) cannot
+    // change a rank decision taken from projected energies; relative to the scaled matrix
+    if (floorAbs) {
+        const double fa = floorFrac * (*floorAbs) * sc;
+        if (fa > (double)floorRel) floorRel = (float)fmin(fa, 1.0);
+    }
     for (int e_ = tid; e_ < m * m; e_ += blockDim.x) {
         const int i = e_ % m, j = e_ / m;
         a[i * S + j] = (i < c && j < c) ? (float)(A64[i * S + j] * sc) : 0.0f;
@@ -625,13 +632,14 @@ size_t gjacobi_smem() {
 
 void launch_gjacobi(cudaStream_t st, int batch, const double* A, int lda, long long bsA,
                     const int* dims, int dstride, int cmax, double* ev, long long bsE,
-                    double* V, int ldv, long long bsV, bool rq, float floorRel)
+                    double* V, int ldv, long long bsV, bool rq, float floorRel,
+                    const double* floorAbs, double floorFrac)
 {
     if (batch <= 0) return;
     const bool prof = prof_active(KC_JACOBI);
     ProfMark mark;
     if (prof) prof_begin(st, mark);
-    note_launch(); gjacobi_kernel<<<batch, kGjThreads, gjacobi_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, rq ? 1 : 0, floorRel, prof ? 1 : 0);
+    note_launch(); gjacobi_kernel<<<batch, kGjThreads, gjacobi_smem(), st>>>(A, lda, bsA, dims, dstride, cmax, ev, bsE, V, ldv, bsV, rq ? 1 : 0, floorRel, prof ? 1 : 0, floorAbs, floorFrac);
     if (prof) prof_end(st, mark);
 }
 
