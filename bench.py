@@ -9,9 +9,12 @@ at the settings that reach relative error 1e-6 (PCG tol 1e-7, truncation eps 1e-
 operator set-up (symbol and preconditioner CP factors, workspace) is done once before timing,
 as a library user would for repeated solves with one operator.  One step solves `--batch`
 problems of the set (64 by default: consecutive slices, round robin, so 8 steps cover the 512
-problems; --batch 512 solves the whole set per step) with fc_solve_batched: a pool of 16 host
+problems; --batch 512 solves the whole set per step) with fc_solve_batched: a pool of host
 threads, each driving one solve at a time on a library worker stream.  Only solves that reach
-the PCG tolerance count toward `value`.
+the PCG tolerance count toward `value`.  Before timing, the library's autotuner
+(fc_autotune_batched) chooses the launch schedule (GEMM tiles and K splits, the tensor-core
+threshold, worker count and problem order) by timing the first slice under each candidate;
+`tuner` reports its choice (--no-tune keeps the default schedule).
 
 Contraction forms (fc_solve_opts.precision on the same handles): fp64 (FP64 throughout), df32
 (double-float FP32 contractions), tc64 (FP64-accurate digit products on the BF16 tensor cores)
@@ -65,6 +68,8 @@ def parse(argv=None):
     p.add_argument("--batch", type=int, default=BATCH_STEP,
                    help="problems per step (slices of the 512-problem set, round robin)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tune", action="store_true",
+                   help="time under the default launch schedule instead of the tuned one")
     p.add_argument("--max-err", type=float, default=1e-6,
                    help="exit status 3 when a sampled solution's error exceeds this")
     return p.parse_args(argv)
@@ -341,6 +346,26 @@ def main(argv=None):
     meets = [f for f in survey if survey[f]["sample_converged"] and
              survey[f]["max_rel_err_vs_full_sample"] <= args.max_err]
     best = max(meets, key=lambda f: survey[f]["value"]) if meets else 0
+    # the autotuner (fc_autotune_batched): tile shapes, K splits, the tensor-core threshold and
+    # the batch policy, each candidate timed on one fc_solve_batched run of the first slice in
+    # the chosen form (outside the timed region); the best becomes the process schedule
+    default_schedule = fc.fc_get_schedule().as_dict()
+    tuner = None
+    if not args.no_tune:
+        _, prec, spectral, _, _ = FORMS[best]
+        idx = slices[0]
+        t_tune = time.perf_counter()
+        sched, cost, evals = fc.fc_autotune_batched(
+            [hs[i] for i in idx], [Bs[i] for i in idx], [Us[i] for i in idx],
+            tol=[probs[i].tol for i in idx], eps=[probs[i].eps for i in idx], precision=prec,
+            spectral=spectral, stall=STALL, passes=1, min_gain=0.02, stream=main_stream)
+        tuner = {"schedule": sched.as_dict(), "default": default_schedule, "evaluations": evals,
+                 "seconds": time.perf_counter() - t_tune,
+                 "first_slice_solves_per_s": {"default (forms survey)": survey[best]["value"],
+                                              "tuned": 1.0 / cost if cost > 0 else None},
+                 "search": "coordinate descent over the schedule fields, one pass, 2 % "
+                           "margin; cost = device seconds per converged solve of one batched "
+                           "run of the first slice"}
     # the headline: warm-up and exactly K timed steps of the chosen form
     counter["step"] = 0
     for _ in range(args.warmup):
@@ -410,10 +435,12 @@ def main(argv=None):
                            "l2": "inputs > L2 (50+ GB of tables and workspaces); also flushed "
                                  "before every timed step (512 MiB write, untimed)",
                            "setup": f"per problem, before timing ({t_setup:.0f} s, 16 threads)",
-                           "concurrency": "fc_solve_batched: 16 host threads, 16 library "
-                                          "worker streams",
+                           "concurrency": f"fc_solve_batched: {fc.fc_get_schedule().workers} "
+                                          "host threads on as many library worker streams",
+                           "schedule": fc.fc_get_schedule().as_dict(),
                            "work_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8")},
                 "forms": forms,
+                "tuner": tuner,
                 "vs_plain_fp64": value / survey[0]["value"] if survey[0]["value"] else None,
                 "pcg_iters_mean": float(np.mean(iters)) if iters else None,
                 "solves_timed": len(statuses),

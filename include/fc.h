@@ -213,10 +213,10 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* opts,
              fc_solve_info* info, void* stream);
 
 /* `count` independent solves (each as fc_solve on its own handle, right-hand side rhs[i],
- * solution u[i], options opts[i] (opts may be NULL), info[i]), run concurrently.  A pool of at
- * most 16 host threads takes the problems in order; each thread drives Algorithm 1 on a
- * non-blocking worker stream of the library's own (16 per device, created on first use, kept
- * until exit).  The worker streams start after the work already queued on `stream`, and
+ * solution u[i], options opts[i] (opts may be NULL), info[i]), run concurrently.  A pool of
+ * host threads (fc_schedule.workers, 16 unless set or tuned) takes the problems in the given
+ * order or largest first (fc_schedule.order); each thread drives Algorithm 1 on a non-blocking
+ * worker stream of the library's own (per device, created on first use, kept until exit).  The worker streams start after the work already queued on `stream`, and
  * `stream` waits for them before later work on it runs; the call returns when every solve has
  * finished.  A single solve keeps only a few of the 152 SMs busy (its small eigen-solves run
  * on one CTA each), so independent problems overlap on the device.  Handles must be pairwise
@@ -227,6 +227,62 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* opts,
  * CUDA_DEVICE_MAX_CONNECTIONS is set (up to 32) before the context is created. */
 int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
                      const fc_solve_opts* opts, fc_solve_info* info, void* stream);
+
+/* Launch schedule of the contraction kernels and of fc_solve_batched, process-wide.  The
+ * paper has no counterpart: these are the tile shapes, K splits and batch policy that the
+ * autotuner below chooses by measurement.  Every schedule gives the same solution up to the
+ * rounding order of the contractions' sums.  Defaults in brackets. */
+typedef struct fc_schedule {
+    int gemm_cover;     /* FP64 / double-float GEMM tile: the largest of 64, 32, 16 whose      */
+                        /* launch has at least gemm_cover * 152 / 8 output tiles (double-float: */
+                        /* a quarter of that); 1..64 [8]                                        */
+    int gemm_split;     /* when those tiles number below 2 * 152, split K (ranges of >= 64)    */
+                        /* until about gemm_split CTAs per SM; 0 = never; 0..16 [4]             */
+    int tc_split;       /* tensor-core contraction: 1 = K ranges spread over the waves of one   */
+                        /* CTA per SM, 0 = fewest K ranges of <= 448; 0..1 [1]                  */
+    int tc_min_log2;    /* contraction form 3 sends contractions of >= 2^tc_min_log2           */
+                        /* multiply-adds to the tensor cores, smaller ones to the FP64 GEMM;   */
+                        /* 10..40 [24]                                                          */
+    int workers;        /* fc_solve_batched host threads and worker streams; 1..64 [16]       */
+    int order;          /* fc_solve_batched: 0 = problems in the given order, 1 = largest n^d  */
+                        /* first (then largest right-hand-side rank); 0..1 [0]                 */
+} fc_schedule;
+
+/* Read / replace the process schedule.  fc_set_schedule returns FC_EINVAL (and changes
+ * nothing) if a field is out of range; it must not be called while a solve runs in another
+ * thread. */
+int fc_get_schedule(fc_schedule* out);
+int fc_set_schedule(const fc_schedule* s);
+
+/* Cost of one candidate schedule for fc_autotune (lower is better; negative, NaN or infinite:
+ * the candidate failed). */
+typedef double (*fc_tune_cost)(const fc_schedule* candidate, void* ctx);
+
+/* The autotuner's search, on any cost: coordinate descent from *start (NULL: the process
+ * schedule).  Each pass visits the fields in declaration order and evaluates every other value
+ * of the field's candidate list with the other fields at their best so far:
+ *   gemm_cover {1, 2, 4, 8, 16}, gemm_split {0, 1, 2, 4, 8}, tc_split {0, 1},
+ *   tc_min_log2 {20, 22, 24, 26}, workers {8, 16, 24, 32}, order {0, 1};
+ * a value is kept when its cost is below (1 - min_gain) times the best cost so far (min_gain in
+ * [0, 1): a margin against timing noise).  Stops after `passes` passes (1..8) or after a pass
+ * that kept nothing.  The process schedule is not changed.  *best, *best_cost and *evals (cost
+ * evaluations, the start's included) may be NULL.  FC_EINVAL: bad arguments, a start out of
+ * range, or a start whose cost failed. */
+int fc_autotune(const fc_schedule* start, int passes, double min_gain, fc_tune_cost cost,
+                void* ctx, fc_schedule* best, double* best_cost, int* evals);
+
+/* The batched form's autotuner: fc_autotune from the process schedule, the cost of a candidate
+ * being one fc_solve_batched run of the given problems under it (the candidate is the process
+ * schedule during that run): elapsed device time on `stream` (CUDA events around the call) in
+ * seconds per converged solve (info status FC_OK); no converged solve is a failed candidate.
+ * One untimed run of the start comes first (first-use set-up of streams and kernels).  At exit
+ * the process schedule is the best found (also in *best); u holds the last run's solutions.
+ * Returns FC_OK, FC_EINVAL (arguments as for fc_solve_batched and fc_autotune), or the first
+ * error other than a solve's own status (FC_ENOCONV, FC_EBREAKDOWN, FC_ENAN are costs, not
+ * errors); on error the process schedule is restored. */
+int fc_autotune_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
+                        const fc_solve_opts* opts, int passes, double min_gain,
+                        fc_schedule* best, double* best_cost, int* evals, void* stream);
 
 /* Expand a CP tensor to the full n^d array, column-major (i_1 fastest). */
 int fc_to_full(fc_handle h, const fc_cp* x, double* dev_dense, void* stream);

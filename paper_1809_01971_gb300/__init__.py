@@ -15,13 +15,13 @@ import os as _os
 
 _os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
-from .fc import (CP, FCError, Handle, fc_apply, fc_apply_trunc, fc_destroy, fc_dgemm, fc_full_solve, fc_get_info,
-                 fc_get_symbol, fc_inner, fc_inner_static, fc_last_cuda_error, fc_launch_count, fc_prof_enable,
-                 fc_prof_read, fc_precond, fc_set_wait_limit, fc_set_workspace, fc_setup, fc_solve, fc_solve_batched, fc_state,
+from .fc import (CP, FCError, Handle, fc_apply, fc_apply_trunc, fc_autotune, fc_autotune_batched, fc_destroy,
+                 fc_dgemm, fc_full_solve, fc_get_info, fc_get_schedule, fc_get_symbol, fc_inner, fc_inner_static, fc_last_cuda_error, fc_launch_count, fc_prof_enable,
+                 fc_prof_read, fc_precond, fc_set_schedule, fc_set_wait_limit, fc_set_workspace, fc_setup, fc_solve, fc_solve_batched, fc_state,
                  fc_strerror, fc_symeig, fc_to_full, fc_truncate, fc_workspace_size, lib)
 
-__all__ = ["CP", "FCError", "Handle", "fc_apply", "fc_apply_trunc", "fc_destroy", "fc_dgemm", "fc_full_solve",
-           "fc_get_info", "fc_get_symbol", "fc_inner", "fc_inner_static", "fc_last_cuda_error",
-           "fc_launch_count", "fc_prof_enable", "fc_prof_read", "fc_precond", "fc_set_wait_limit", "fc_set_workspace",
+__all__ = ["CP", "FCError", "Handle", "fc_apply", "fc_apply_trunc", "fc_autotune", "fc_autotune_batched",
+           "fc_destroy", "fc_dgemm", "fc_full_solve", "fc_get_info", "fc_get_schedule", "fc_get_symbol", "fc_inner", "fc_inner_static", "fc_last_cuda_error",
+           "fc_launch_count", "fc_prof_enable", "fc_prof_read", "fc_precond", "fc_set_schedule", "fc_set_wait_limit", "fc_set_workspace",
            "fc_setup", "fc_solve", "fc_solve_batched", "fc_state", "fc_strerror", "fc_symeig",
            "fc_to_full", "fc_truncate", "fc_workspace_size", "lib"]

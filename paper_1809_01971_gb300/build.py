@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfc.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["api.cu", "k_fft.cu", "k_linalg.cu", "k_symeig.cu", "k_tensor.cu", "noalloc.cu"]
+CU = ["api.cu", "k_fft.cu", "k_linalg.cu", "k_symeig.cu", "k_tensor.cu", "noalloc.cu", "tune.cu"]
 CPP = ["setup_host.cpp"]
 
 

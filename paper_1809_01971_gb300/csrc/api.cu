@@ -22,6 +22,7 @@ using namespace fc;
 #include <atomic>
 
 namespace fc {
+SchedState g_sched;
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -1333,33 +1334,57 @@ int fc_solve(fc_handle h, const fc_cp* rhs, fc_cp* u, const fc_solve_opts* o,
     return finish(FC_ENOCONV);
 }
 
-// Host threads of fc_solve_batched: enough to keep the GPU busy with latency-bound solves,
-// few enough not to oversubscribe the host (16 cores on the GB300 machines).
-constexpr int kBatchWorkers = 16;
+// Host threads of fc_solve_batched: at most kMaxWorkers (the schedule's `workers`, 16 unless
+// set or tuned: enough to keep the GPU busy with latency-bound solves, few enough not to
+// oversubscribe the host's cores).
+constexpr int kMaxWorkers = 64;
 
 namespace {
-// One non-blocking stream per batch worker and device, created on first use and kept for the
-// life of the process (a solve is a chain of small launches and host synchronisations on its
-// worker's stream).
+// Non-blocking streams of the batch workers per device, created on first use and kept for
+// the life of the process (a solve is a chain of small launches and host synchronisations on
+// its worker's stream).
 struct WorkerStreams {
     std::mutex mu;
-    cudaStream_t s[64][kBatchWorkers] = {};
-    bool made[64] = {};
+    cudaStream_t s[64][kMaxWorkers] = {};
+    int made[64] = {};
 };
 WorkerStreams g_workers;
 
-int worker_streams(int dev, cudaStream_t* out) {
-    if (dev < 0 || dev >= 64) return FC_EINVAL;
+int worker_streams(int dev, int count, cudaStream_t* out) {
+    if (dev < 0 || dev >= 64 || count < 1 || count > kMaxWorkers) return FC_EINVAL;
     std::lock_guard<std::mutex> lock(g_workers.mu);
-    if (!g_workers.made[dev]) {
-        for (int i = 0; i < kBatchWorkers; ++i)
-            CK(cudaStreamCreateWithFlags(&g_workers.s[dev][i], cudaStreamNonBlocking));
-        g_workers.made[dev] = true;
-    }
-    for (int i = 0; i < kBatchWorkers; ++i) out[i] = g_workers.s[dev][i];
+    for (; g_workers.made[dev] < count; ++g_workers.made[dev])
+        CK(cudaStreamCreateWithFlags(&g_workers.s[dev][g_workers.made[dev]], cudaStreamNonBlocking));
+    for (int i = 0; i < count; ++i) out[i] = g_workers.s[dev][i];
     return FC_OK;
 }
 }  // namespace
+
+int fc_get_schedule(fc_schedule* out) {
+    if (!out) return FC_EINVAL;
+    out->gemm_cover = sched(g_sched.gemm_cover);
+    out->gemm_split = sched(g_sched.gemm_split);
+    out->tc_split = sched(g_sched.tc_split);
+    out->tc_min_log2 = sched(g_sched.tc_min_log2);
+    out->workers = sched(g_sched.workers);
+    out->order = sched(g_sched.order);
+    return FC_OK;
+}
+
+int fc_set_schedule(const fc_schedule* s) {
+    if (!s) return FC_EINVAL;
+    if (s->gemm_cover < 1 || s->gemm_cover > 64 || s->gemm_split < 0 || s->gemm_split > 16 ||
+        s->tc_split < 0 || s->tc_split > 1 || s->tc_min_log2 < 10 || s->tc_min_log2 > 40 ||
+        s->workers < 1 || s->workers > kMaxWorkers || s->order < 0 || s->order > 1)
+        return FC_EINVAL;
+    g_sched.gemm_cover.store(s->gemm_cover);
+    g_sched.gemm_split.store(s->gemm_split);
+    g_sched.tc_split.store(s->tc_split);
+    g_sched.tc_min_log2.store(s->tc_min_log2);
+    g_sched.workers.store(s->workers);
+    g_sched.order.store(s->order);
+    return FC_OK;
+}
 
 int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
                      const fc_solve_opts* opts, fc_solve_info* info, void* stream) {
@@ -1372,9 +1397,20 @@ int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
     if (count == 0) return FC_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FC_ECUDA;
-    cudaStream_t ws[kBatchWorkers];
-    if (int rc = worker_streams(dev, ws)) return rc;
-    const int nworkers = std::min(count, kBatchWorkers);
+    const int nworkers = std::min(count, std::max(1, sched(g_sched.workers)));
+    cudaStream_t ws[kMaxWorkers];
+    if (int rc = worker_streams(dev, nworkers, ws)) return rc;
+    // the order the workers take the problems in: as given, or (schedule field order) the
+    // largest first, n^d then right-hand-side rank, so that no large solve starts last
+    std::vector<int> seq(count);
+    for (int i = 0; i < count; ++i) seq[i] = i;
+    if (sched(g_sched.order) == 1) {
+        auto size = [&](int i) { return std::pow((double)h[i]->n, h[i]->d); };
+        std::stable_sort(seq.begin(), seq.end(), [&](int a, int b) {
+            if (size(a) != size(b)) return size(a) > size(b);
+            return rhs[a].rank > rhs[b].rank;
+        });
+    }
     // fork: every worker stream starts after the work already queued on the caller's stream
     cudaStream_t caller = (cudaStream_t)stream;
     cudaEvent_t fork;
@@ -1390,10 +1426,11 @@ int fc_solve_batched(int count, const fc_handle* h, const fc_cp* rhs, fc_cp* u,
     for (int w_ = 0; w_ < nworkers; ++w_)
         workers.emplace_back([&, w_]() {
             if (cudaSetDevice(dev) != cudaSuccess) {
-                for (int i; (i = next.fetch_add(1)) < count;) rc[i] = FC_ECUDA;
+                for (int q; (q = next.fetch_add(1)) < count;) rc[seq[q]] = FC_ECUDA;
                 return;
             }
-            for (int i; (i = next.fetch_add(1)) < count;) {
+            for (int q; (q = next.fetch_add(1)) < count;) {
+                const int i = seq[q];
                 std::memset(&info[i], 0, sizeof(fc_solve_info));
                 rc[i] = fc_solve(h[i], &rhs[i], &u[i], opts ? &opts[i] : nullptr, &info[i], ws[w_]);
                 if (rc[i] != FC_OK && info[i].status == FC_OK) info[i].status = rc[i];

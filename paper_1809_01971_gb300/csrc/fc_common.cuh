@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <algorithm>
+#include <atomic>
 
 #define FC_DEV __device__ __forceinline__
 
@@ -22,6 +23,21 @@ bool prof_active(int kclass);
 void prof_begin(cudaStream_t st, ProfMark& m);
 void prof_end(cudaStream_t st, const ProfMark& m);
 unsigned long long* prof_work_counter();   // device counter of the class's algorithmic flops
+
+// Launch schedule (fc_schedule in fc.h): the tile and split rules of the contraction launches
+// and the policy of fc_solve_batched, set by fc_set_schedule or chosen by fc_autotune.  Each
+// field is read on its own at every launch (relaxed loads; fc_set_schedule is not called
+// while solves run).
+struct SchedState {
+    std::atomic<int> gemm_cover{8};     // FP64 GEMM tiles: cover gemm_cover / 8 of the SMs
+    std::atomic<int> gemm_split{4};     // split-K until about gemm_split CTAs per SM (0: never)
+    std::atomic<int> tc_split{1};       // tensor-core K ranges: 1 fill the waves, 0 fewest
+    std::atomic<int> tc_min_log2{24};   // form 3: tensor cores from 2^tc_min_log2 multiply-adds
+    std::atomic<int> workers{16};       // fc_solve_batched host threads / worker streams
+    std::atomic<int> order{0};          // fc_solve_batched: 0 given order, 1 largest first
+};
+extern SchedState g_sched;
+inline int sched(const std::atomic<int>& f) { return f.load(std::memory_order_relaxed); }
 
 constexpr int kMaxC = 64;       // largest dense eigen / Cholesky problem handled by one CTA
 constexpr int kThreads = 256;
@@ -332,15 +348,16 @@ __global__ void gemm_prescale_kernel(int M, int N, const int* dM, const int* dN,
 #include "fc_tc.cuh"
 namespace fc {
 
-// Launch: the largest tile (64, 32, 16) whose grid still covers the 152 SMs, then split-K
-// until about 4 CTAs per SM (GB300 runs few FP64 FMAs per SM per clock, so the SM count
-// decides the rate).
+// Launch (rules of the schedule, defaults in brackets): the largest tile (64, 32, 16) whose
+// grid still has gemm_cover / 8 [1] tiles per SM, then, for grids below two tiles per SM,
+// split-K until about gemm_split [4] CTAs per SM (GB300 runs few FP64 FMAs per SM per clock,
+// so for one solve alone the SM count decides the rate; with many solves in flight larger
+// tiles and fewer splits waste less).
 // Precision of a contraction: FP64, double-float on the FP32 pipe (gemm_df_kernel), or
 // FP64-accurate digit products on the BF16 tensor cores (gemm_tc_kernel) for contractions
-// of at least kTcMinMacs multiply-adds (smaller ones stay on the FP64 kernel, whose latency
-// is lower).
+// of at least 2^tc_min_log2 [2^24] multiply-adds (smaller ones stay on the FP64 kernel,
+// whose latency is lower).
 enum GemmPrec { GP_F64 = 0, GP_DF32 = 1, GP_TC64 = 2 };
-constexpr long long kTcMinMacs = 1ll << 24;
 
 template <class LA, class LB>
 inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, double alpha,
@@ -348,7 +365,7 @@ inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, d
                    const int* dM = nullptr, const int* dN = nullptr, const int* dK = nullptr)
 {
     if (M <= 0 || N <= 0 || batch <= 0) return;
-    if (prec == GP_TC64 && (long long)M * N * K * batch >= kTcMinMacs &&
+    if (prec == GP_TC64 && (long long)M * N * K * batch >= (1ll << sched(g_sched.tc_min_log2)) &&
         gemm_tc(st, M, N, K, A, B, alpha, beta, C, ldc, bsC, batch, dM, dN, dK))
         return;
     auto tiles_of = [&](int T) {
@@ -357,12 +374,14 @@ inline void gemm_p(int prec, cudaStream_t st, int M, int N, int K, LA A, LB B, d
     // FP64: the largest tile that still covers the SMs.  Double-float: operand splitting
     // costs FP64 work per loaded element, so keep 64-wide tiles down to a quarter of the SMs.
     int T = 64;
-    const long long need = (prec == GP_DF32) ? kNumSMs / 4 : kNumSMs;
+    const long long cover = sched(g_sched.gemm_cover);
+    const long long need = std::max(1ll, kNumSMs * cover / ((prec == GP_DF32) ? 32 : 8));
     if (tiles_of(64) < need) T = (tiles_of(32) < need) ? 16 : 32;
     const long long tiles = tiles_of(T);
     int splits = 1;
-    if (tiles < 2 * kNumSMs && K >= 128) {
-        long long want = (4 * kNumSMs + tiles - 1) / tiles;
+    const long long spl = sched(g_sched.gemm_split);
+    if (spl > 0 && tiles < 2 * kNumSMs && K >= 128) {
+        long long want = (spl * kNumSMs + tiles - 1) / tiles;
         long long most = (K + 63) / 64;            // at least 64 of K per split
         splits = (int)std::min<long long>(std::min(want, most), 64);
     }

@@ -598,12 +598,14 @@ inline bool gemm_tc(cudaStream_t st, int M, int N, int K, LA A, LB B, double alp
     if (M <= 0 || N <= 0 || batch <= 0) return true;
     const int BN = (N <= 16) ? 16 : (N <= 32) ? 32 : (N <= 48) ? 48 : 64;
     const long long tiles = (long long)((M + kTcBM - 1) / kTcBM) * ((N + BN - 1) / BN) * batch;
-    // fewest K ranges of at most kTcKC, then as many as fill the waves of one CTA per SM
-    // (at least 64 of K each)
+    // fewest K ranges of at most kTcKC, then (schedule field tc_split) as many as fill the
+    // waves of one CTA per SM (at least 64 of K each)
     const int smin = std::max(1, (K + kTcKC - 1) / kTcKC);
     const long long waves = (tiles * smin + kNumSMs - 1) / kNumSMs;
-    int splits = (int)std::max<long long>(
-        smin, std::min<long long>(waves * kNumSMs / tiles, std::max(1, (K + 63) / 64)));
+    int splits = smin;
+    if (sched(g_sched.tc_split))
+        splits = (int)std::max<long long>(
+            smin, std::min<long long>(waves * kNumSMs / tiles, std::max(1, (K + 63) / 64)));
     int kchunk = (K + splits - 1) / splits;
     kchunk = (kchunk + kTcKS - 1) / kTcKS * kTcKS;
     if (kchunk > kTcKC) kchunk = kTcKC;

@@ -69,6 +69,18 @@ class fc_solve_info(C.Structure):
                 ("history", C.c_double * 128)]
 
 
+class fc_schedule(C.Structure):
+    _fields_ = [("gemm_cover", C.c_int), ("gemm_split", C.c_int), ("tc_split", C.c_int),
+                ("tc_min_log2", C.c_int), ("workers", C.c_int), ("order", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# cost callback of fc_autotune: double (*)(const fc_schedule*, void*)
+TUNE_COST = C.CFUNCTYPE(C.c_double, C.POINTER(fc_schedule), C.c_void_p)
+
+
 class FCError(RuntimeError):
     def __init__(self, fn: str, code: int, msg: str):
         super().__init__(f"{fn}: {msg} ({code})")
@@ -115,6 +127,13 @@ def lib() -> C.CDLL:
             "fc_symeig": (I, [I, I, I, V, I, C.c_longlong, V, C.c_longlong, V, I, C.c_longlong, V]),
             "fc_prof_read": (I, [C.POINTER(C.c_longlong), C.POINTER(D), C.POINTER(D)]),
             "fc_dgemm": (I, [I, I, I, I, I, I, D, V, I, V, I, D, V, I, V]),
+            "fc_get_schedule": (I, [C.POINTER(fc_schedule)]),
+            "fc_set_schedule": (I, [C.POINTER(fc_schedule)]),
+            "fc_autotune": (I, [C.POINTER(fc_schedule), I, D, TUNE_COST, V,
+                                C.POINTER(fc_schedule), C.POINTER(D), C.POINTER(I)]),
+            "fc_autotune_batched": (I, [I, C.POINTER(P), cp_p, cp_p, C.POINTER(fc_solve_opts), I,
+                                        D, C.POINTER(fc_schedule), C.POINTER(D), C.POINTER(I),
+                                        V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -369,12 +388,7 @@ def fc_solve(h: Handle, rhs: CP, u: CP, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
     return info
 
 
-def fc_solve_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
-                     raise_on_fail: bool = True, spectral: bool = False, precision=None,
-                     stream=None, stall: int = 0):
-    """Independent solves run concurrently (a pool of up to 16 host threads, each on a worker
-    stream of the library that starts after the work queued on ``stream`` and joins it).
-    tol / eps / kmax / max_rank / precision are scalars or per-problem sequences."""
+def _batch_args(handles, rhs, us, tol, eps, kmax, max_rank, spectral, precision, stall):
     count = len(handles)
 
     def per(v):
@@ -388,6 +402,17 @@ def fc_solve_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
                                                 int(mrs[i]), 1 if spectral else 0, _form(prs[i]),
                                                 int(stall))
                                   for i in range(count)])
+    return count, H, R, Uc, O
+
+
+def fc_solve_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
+                     raise_on_fail: bool = True, spectral: bool = False, precision=None,
+                     stream=None, stall: int = 0):
+    """Independent solves run concurrently (a pool of host threads, fc_schedule.workers, each
+    on a worker stream of the library that starts after the work queued on ``stream`` and
+    joins it).  tol / eps / kmax / max_rank / precision are scalars or per-problem sequences."""
+    count, H, R, Uc, O = _batch_args(handles, rhs, us, tol, eps, kmax, max_rank, spectral,
+                                     precision, stall)
     infos = (fc_solve_info * count)()
     rc = lib().fc_solve_batched(count, H, R, Uc, O, infos, _stream(stream))
     for i in range(count):
@@ -395,6 +420,60 @@ def fc_solve_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
     if raise_on_fail or rc not in (FC_ENOCONV, FC_EBREAKDOWN, FC_ENAN):
         _check("fc_solve_batched", rc)
     return list(infos)
+
+
+def fc_get_schedule() -> fc_schedule:
+    """The process launch schedule (tile and split rules, batch policy)."""
+    s = fc_schedule()
+    _check("fc_get_schedule", lib().fc_get_schedule(C.byref(s)))
+    return s
+
+
+def fc_set_schedule(s=None, **fields) -> fc_schedule:
+    """Replace the process schedule by ``s`` (default: the current one) with ``fields``
+    changed; returns the previous schedule."""
+    prev = fc_get_schedule()
+    new = fc_schedule(*[getattr(s if s is not None else prev, k) for k, _ in fc_schedule._fields_])
+    for k, v in fields.items():
+        if k not in dict(fc_schedule._fields_):
+            raise TypeError(f"no schedule field {k!r}")
+        setattr(new, k, int(v))
+    _check("fc_set_schedule", lib().fc_set_schedule(C.byref(new)))
+    return prev
+
+
+def fc_autotune(cost, start=None, passes: int = 1, min_gain: float = 0.02):
+    """The autotuner's coordinate descent on a Python cost ``cost(schedule_dict) -> float``;
+    returns (best schedule, best cost, evaluations).  The process schedule is not changed."""
+    def _cb(cand, _ctx):
+        try:
+            return float(cost(cand.contents.as_dict()))
+        except Exception:       # a failed candidate
+            return float("nan")
+
+    cb = TUNE_COST(_cb)
+    best, bc, ev = fc_schedule(), C.c_double(), C.c_int()
+    _check("fc_autotune", lib().fc_autotune(C.byref(start) if start is not None else None,
+                                            int(passes), float(min_gain), cb, None,
+                                            C.byref(best), C.byref(bc), C.byref(ev)))
+    return best, bc.value, ev.value
+
+
+def fc_autotune_batched(handles, rhs, us, tol=1e-8, eps=0.0, kmax=100, max_rank=0,
+                        spectral: bool = False, precision=None, stall: int = 0, passes: int = 1,
+                        min_gain: float = 0.02, stream=None):
+    """The batched form's autotuner: every candidate schedule timed on one fc_solve_batched run
+    of these problems (seconds per converged solve); leaves the best as the process schedule
+    and returns (best schedule, its cost, evaluations)."""
+    count, H, R, Uc, O = _batch_args(handles, rhs, us, tol, eps, kmax, max_rank, spectral,
+                                     precision, stall)
+    best, bc, ev = fc_schedule(), C.c_double(), C.c_int()
+    rc = lib().fc_autotune_batched(count, H, R, Uc, O, int(passes), float(min_gain),
+                                   C.byref(best), C.byref(bc), C.byref(ev), _stream(stream))
+    for i in range(count):
+        us[i].rank = Uc[i].rank
+    _check("fc_autotune_batched", rc)
+    return best, bc.value, ev.value
 
 
 def fc_set_wait_limit(iterations: int) -> int:
