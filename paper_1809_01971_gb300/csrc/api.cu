@@ -450,6 +450,10 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     const int c = sketch ? CM : (int)Kt;
     const int cs = sketch ? CM - kHold : c;
     const unsigned long long seed = (h->seed += 0x9E3779B97F4A7C15ull);
+    // contraction form of the n-sized products of the truncation (sketches, Cholesky-QR Grams
+    // and bases, the Ritz basis, the output factors): the tensor-core digits in form 3, FP64
+    // otherwise (the orthonormalisation needs FP64-accurate Grams, which double-float is not)
+    const int bp = (h->prec == GP_TC64) ? GP_TC64 : GP_F64;
     int* dims = w.dims;
     CK(cudaMemsetAsync(dims, 0, sizeof(int) * D_FLAG, st));
     CK(cudaMemsetAsync(w.scal, 0, sizeof(double) * 64, st));
@@ -460,13 +464,13 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
             launch_kr_cols(st, d, n, kr->rE, kr->S, kr->Et, n, kr->bsEt, nullptr,
                            kr->Yh, n, (long long)n * h->KIN, kr->xb, 1, w.Y, n, nC);
         else
-            launch_sketch_kr(st, d, n, kr->rE, kr->S, c, kr->Et, n, kr->bsEt, nullptr,
+            launch_sketch_kr(st, bp, d, n, kr->rE, kr->S, c, kr->Et, n, kr->bsEt, nullptr,
                              kr->Yh, n, (long long)n * h->KIN, kr->xb, seed, w.Y, n, nC, w.tmp);
     } else {
         if (!sketch)
             launch_scale_cols_abs(st, d, n, (int)K, dn->U, dn->ld, dn->bs, dn->w, w.Y, n, nC);
         else
-            launch_sketch_dense(st, d, n, (int)K, c, dn->U, dn->ld, dn->bs, dn->w, seed, w.Y, n, nC);
+            launch_sketch_dense(st, bp, d, n, (int)K, c, dn->U, dn->ld, dn->bs, dn->w, seed, w.Y, n, nC);
     }
     CKL();
     // Orthonormal basis of range(Y[:, :cs]) by pivoted Cholesky-QR with one deflation level.
@@ -476,21 +480,21 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     // appended to Q1 and re-orthonormalised (span preserved to ~1e-15 relative).
     const long long CC = (long long)CM * CM;
     auto cholqr = [&](const double* src, double* dst, int* rk) {
-        gemm(st, cs, cs, n, LdT{src, n, nC}, LdN{src, n, nC}, 1.0, 0.0, w.M, CM, CC, d);
+        gemm_p(bp, st, cs, cs, n, LdT{src, n, nC}, LdN{src, n, nC}, 1.0, 0.0, w.M, CM, CC, d);
         launch_pchol(st, d, w.M, CM, CC, nullptr, 0, cs, 1e-15, w.Tm, CM, CC, rk, 1);
-        gemm(st, n, cs, cs, LdN{src, n, nC}, LdN{w.Tm, CM, CC}, 1.0, 0.0, dst, n, nC, d);
+        gemm_p(bp, st, n, cs, cs, LdN{src, n, nC}, LdN{w.Tm, CM, CC}, 1.0, 0.0, dst, n, nC, d);
     };
     cholqr(w.Y, w.Q, dims + D_C1);           // Q1 (orthogonal to ~kappa^2 u)
     cholqr(w.Q, w.Y2, dims + D_C1);          // Q1 re-orthonormalised
     // remainder tmp = Y - Q1 (Q1^T Y), columns scaled to unit norm (zero if at rounding level)
-    gemm(st, cs, cs, n, LdT{w.Y2, n, nC}, LdN{w.Y, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+    gemm_p(bp, st, cs, cs, n, LdT{w.Y2, n, nC}, LdN{w.Y, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
     CK(cudaMemcpyAsync(w.tmp, w.Y, sizeof(double) * d * nC, cudaMemcpyDeviceToDevice, st));
-    gemm(st, n, cs, cs, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.tmp, n, nC, d);
+    gemm_p(bp, st, n, cs, cs, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.tmp, n, nC, d);
     launch_deflate_normalize(st, d, n, cs, w.tmp, n, nC, w.Y, 1e-13);
     cholqr(w.tmp, w.Q, dims + D_CR);         // Q2
     // Q2 <- Q2 - Q1 (Q1^T Q2), re-orthonormalised
-    gemm(st, cs, cs, n, LdT{w.Y2, n, nC}, LdN{w.Q, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
-    gemm(st, n, cs, cs, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.Q, n, nC, d);
+    gemm_p(bp, st, cs, cs, n, LdT{w.Y2, n, nC}, LdN{w.Q, n, nC}, 1.0, 0.0, w.Tr, CM, CC, d);
+    gemm_p(bp, st, n, cs, cs, LdN{w.Y2, n, nC}, LdN{w.Tr, CM, CC}, -1.0, 1.0, w.Q, n, nC, d);
     cholqr(w.Q, w.GQ, dims + D_CR);
     // [Q1 | Q2] and a final pass; live columns of the basis -> dims[D_C1 + l]
     launch_combine_cols(st, d, n, cs, w.Y2, n, nC, w.GQ, dims + D_C1, dims + D_CR, dims + D_CT);
@@ -555,7 +559,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     launch_gjacobi(st, d, w.Tr, CM, CC, dims + D_C1, 1, cs, w.theta, CM, w.Vr, CM, CC, false,
                    1e-20f, w.scal + 4, kEnergyFloor * eps * eps / (2.0 * d));
     // Zc_l = Q_l Vr_l (all cs Ritz directions, descending)
-    gemm(st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
+    gemm_p(bp, st, n, cs, cs, LdN{Qb, n, nC}, LdN{w.Vr, CM, CC}, 1.0, 0.0, w.Z, n, nC, d);
     // B2_l = Zc_l^T U_l (cs x K, unweighted): its first r_l rows are the projected factors C_l
     // of the core; rho_i = sum_K w_K^2 B2[i, K]^2 is the energy of W_l along Ritz direction i
     const double* wK = dn ? dn->w : w.wK;
@@ -633,8 +637,8 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
         Zuse = w.Zr;
     }
     for (int l = 0; l < d; ++l)
-        gemm(st, n, maxq, RM, LdN{Zuse + l * nC, n, 0}, LdN{w.X + l * RQ, RM, 0}, 1.0, 0.0,
-             out.U[l], out.ld, 0, 1, nullptr, dims + D_Q, dims + D_R + l);
+        gemm_p(bp, st, n, maxq, RM, LdN{Zuse + l * nC, n, 0}, LdN{w.X + l * RQ, RM, 0}, 1.0, 0.0,
+               out.U[l], out.ld, 0, 1, nullptr, dims + D_Q, dims + D_R + l);
     CK(cudaMemcpyAsync(out.xi, w.sigma, sizeof(double) * maxq, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->hint, dims, sizeof(int) * D_SIZE, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -70,14 +70,15 @@ void launch_kr_cols(cudaStream_t st, int d, int n, int Ra, int S, const double* 
                     long long bsE, const double* xa, const double* Yh, int ldy, long long bsY,
                     const double* xb, int absw, double* Y, int ldo, long long bsO);
 // Y = (U diag|w|) Omega, Omega[k,t] ~ N(0,1) from a counter-based hash (seed, mode, k, t)
-void launch_sketch_dense(cudaStream_t st, int d, int n, int K, int c, const double* U, int ldu,
-                         long long bsU, const double* w, unsigned long long seed, double* Y,
-                         int ldy, long long bsY);
-// Y = (E diag|xa| Oa) . (Yh diag|xb| Ob) with Gaussian Oa (Ra x c), Ob (S x c)
-void launch_sketch_kr(cudaStream_t st, int d, int n, int Ra, int S, int c, const double* E,
-                      int lde, long long bsE, const double* xa, const double* Yh, int ldy,
-                      long long bsY, const double* xb, unsigned long long seed, double* Y,
-                      int ldo, long long bsO, double* tmp);
+void launch_sketch_dense(cudaStream_t st, int prec, int d, int n, int K, int c, const double* U,
+                         int ldu, long long bsU, const double* w, unsigned long long seed,
+                         double* Y, int ldy, long long bsY);
+// Y = (E diag|xa| Oa) . (Yh diag|xb| Ob) with Gaussian Oa (Ra x c), Ob (S x c); both sketch
+// launches take the contraction form (GemmPrec) of their GEMMs
+void launch_sketch_kr(cudaStream_t st, int prec, int d, int n, int Ra, int S, int c,
+                      const double* E, int lde, long long bsE, const double* xa, const double* Yh,
+                      int ldy, long long bsY, const double* xb, unsigned long long seed,
+                      double* Y, int ldo, long long bsO, double* tmp);
 // Yr = Y - Q P (deflation), then columns of Yr scaled to unit norm (zero if tiny)
 void launch_deflate_normalize(cudaStream_t st, int d, int n, int c, double* Yr, int ld,
                               long long bs, const double* Yorig, double relTiny);

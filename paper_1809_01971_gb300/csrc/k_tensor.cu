@@ -193,13 +193,13 @@ struct LdGauss {
     }
 };
 
-void launch_sketch_dense(cudaStream_t st, int d, int n, int K, int c, const double* U, int ldu,
-                         long long bsU, const double* w, unsigned long long seed, double* Y,
-                         int ldy, long long bsY)
+void launch_sketch_dense(cudaStream_t st, int prec, int d, int n, int K, int c, const double* U,
+                         int ldu, long long bsU, const double* w, unsigned long long seed,
+                         double* Y, int ldy, long long bsY)
 {
     LdN A{U, ldu, bsU};
     LdGauss B{seed, w};
-    gemm(st, n, c, K, A, B, 1.0, 0.0, Y, ldy, bsY, d);
+    gemm_p(prec, st, n, c, K, A, B, 1.0, 0.0, Y, ldy, bsY, d);
 }
 
 __global__ void hadamard_kernel(long long count, int n, int c, double* Y, int ldy, long long bsY,
@@ -213,15 +213,15 @@ __global__ void hadamard_kernel(long long count, int n, int c, double* Y, int ld
     }
 }
 
-void launch_sketch_kr(cudaStream_t st, int d, int n, int Ra, int S, int c, const double* E,
-                      int lde, long long bsE, const double* xa, const double* Yh, int ldy,
-                      long long bsY, const double* xb, unsigned long long seed, double* Y,
-                      int ldo, long long bsO, double* tmp)
+void launch_sketch_kr(cudaStream_t st, int prec, int d, int n, int Ra, int S, int c,
+                      const double* E, int lde, long long bsE, const double* xa, const double* Yh,
+                      int ldy, long long bsY, const double* xb, unsigned long long seed,
+                      double* Y, int ldo, long long bsO, double* tmp)
 {
     // Y = E diag|xa| Oa ; tmp = Yh diag|xb| Ob ; Y .= tmp   (Khatri-Rao structured sketch)
-    gemm(st, n, c, Ra, LdN{E, lde, bsE}, LdGauss{seed, xa}, 1.0, 0.0, Y, ldo, bsO, d);
-    gemm(st, n, c, S, LdN{Yh, ldy, bsY}, LdGauss{seed ^ 0x5bd1e995ull, xb}, 1.0, 0.0, tmp, ldo,
-         bsO, d);
+    gemm_p(prec, st, n, c, Ra, LdN{E, lde, bsE}, LdGauss{seed, xa}, 1.0, 0.0, Y, ldo, bsO, d);
+    gemm_p(prec, st, n, c, S, LdN{Yh, ldy, bsY}, LdGauss{seed ^ 0x5bd1e995ull, xb}, 1.0, 0.0,
+           tmp, ldo, bsO, d);
     long long cnt = (long long)n * c;
     int blocks = (int)((cnt + 255) / 256);
     if (blocks > 1024) blocks = 1024;
