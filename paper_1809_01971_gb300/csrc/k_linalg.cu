@@ -188,7 +188,7 @@ select_terms_kernel(const double* mu, int ldmu, const int* nslice, const int* np
                     double* sigma, int* tslice, int* tidx, double* dropped)
 {
     __shared__ double key[4096];
-    __shared__ int val[4096];
+    __shared__ short val[4096];                 // candidate index (< 4096), -1 for padding
     const int ns = min(*nslice, smax), np = min(*nper, pmax);
     const int tot = ns * np;
     int P = 1;
@@ -197,7 +197,7 @@ select_terms_kernel(const double* mu, int ldmu, const int* nslice, const int* np
         if (e < tot) {
             int s = e / np, i = e - s * np;
             key[e] = fmax(mu[(long long)s * ldmu + i], 0.0);
-            val[e] = e;
+            val[e] = (short)e;
         } else { key[e] = -1.0; val[e] = -1; }
     }
     __syncthreads();
@@ -209,7 +209,7 @@ select_terms_kernel(const double* mu, int ldmu, const int* nslice, const int* np
                 if (o > e) {
                     bool desc = ((e & k) == 0);
                     double ke = key[e], ko = key[o];
-                    int ve = val[e], vo = val[o];
+                    short ve = val[e], vo = val[o];
                     bool eFirst = (ke > ko) || (ke == ko && ve < vo);
                     bool swap = desc ? !eFirst : eFirst;
                     if (swap) { key[e] = ko; key[o] = ke; val[e] = vo; val[o] = ve; }
@@ -218,21 +218,57 @@ select_terms_kernel(const double* mu, int ldmu, const int* nslice, const int* np
             __syncthreads();
         }
     }
-    if (threadIdx.x == 0) {
-        double thr = frac2 * (*core_e);
-        // suffix sums from the end: drop while cumulative tail <= thr
-        int q = tot;
-        double tail = 0.0;
-        while (q > 0 && tail + key[q - 1] <= thr) { tail += key[q - 1]; --q; }
-        if (q < 1 && tot > 0 && key[0] > 0.0) q = 1;
-        while (q > maxq) { tail += key[q - 1]; --q; }
-        // never keep zero-energy terms
-        while (q > 0 && !(key[q - 1] > 0.0)) --q;
-        *q_out = q;
-        *dropped = tail;
+    // Tails T[t] = sum_{t' >= t} key[t'] of the sorted energies (block-wide suffix scan: each
+    // thread owns kPer consecutive entries, T[tot] = 0).  The terms kept are the shortest
+    // prefix whose tail is within thr (T is non-increasing, so the first t with T[t] <= thr),
+    // at least one term if any energy is positive, at most maxq, and no zero-energy term.
+    constexpr int kPer = 4;                     // 4096 entries / 1024 threads
+    __shared__ double wsum[32];
+    __shared__ int s_first, s_pos;
+    __shared__ double s_tail;
+    const double thr = frac2 * (*core_e);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int e0 = tid * kPer;
+    double own = 0.0;
+    for (int u = 0; u < kPer; ++u)
+        if (e0 + u < tot) own += key[e0 + u];
+    // inclusive suffix within the warp, then the sums of the warps after this one
+    double suf = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_down_sync(0xffffffffu, suf, o);
+        if (lane + o < 32) suf += v;
+    }
+    if (lane == 0) wsum[wid] = suf;
+    if (tid == 0) { s_first = tot; s_pos = tot; }
+    __syncthreads();
+    double after = suf - own;                   // entries of later threads in this warp
+    for (int w2 = wid + 1; w2 < nw; ++w2) after += wsum[w2];
+    double T[kPer];
+    double run = after;
+    for (int u = kPer - 1; u >= 0; --u) {
+        const int e = e0 + u;
+        if (e < tot) run += key[e];
+        T[u] = run;                             // T[e0 + u]
+    }
+    for (int u = 0; u < kPer; ++u) {
+        const int e = e0 + u;
+        if (e >= tot) break;
+        if (T[u] <= thr) atomicMin(&s_first, e);
+        if (!(key[e] > 0.0)) atomicMin(&s_pos, e);
     }
     __syncthreads();
-    const int q = *q_out;
+    int q = s_first;
+    if (q < 1 && tot > 0 && key[0] > 0.0) q = 1;
+    if (q > maxq) q = maxq;
+    if (tid == 0 && q >= tot) s_tail = 0.0;
+    if (q >= e0 && q < e0 + kPer && q < tot) s_tail = T[q - e0];
+    q = min(q, s_pos);                          // zero-energy terms drop for free
+    __syncthreads();
+    if (tid == 0) {
+        *q_out = q;
+        *dropped = s_tail;
+    }
     for (int t = threadIdx.x; t < q; t += blockDim.x) {
         int e = val[t];
         int s = e / np;
