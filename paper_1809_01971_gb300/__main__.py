@@ -57,7 +57,7 @@ def main(argv=None) -> int:
             torch.cuda.nvtx.range_push("fc_solve")
             e0.record(stream)
             info = fc.fc_solve(h, B, U, tol=prob.tol, eps=prob.eps, spectral=args.spectral,
-                               stall=8 if args.batch else 0, raise_on_fail=False)
+                               stall=3 if args.batch else 0, raise_on_fail=False)
             e1.record(stream)
             e1.synchronize()
             torch.cuda.nvtx.range_pop()
