@@ -12,118 +12,145 @@ namespace fc {
 // Diagonal pivoting stops when the largest remaining diagonal is <= relTol * max diag(M);
 // with rank r and pivot order piv, Y P[:, :r] = Q R11, and T[:, :r] = P[:, :r] R11^{-1}
 // (T zero elsewhere) gives Q = Y T with orthonormal first r columns.  rank[b*rstride] = r.
-// One warp per matrix: the factorisation is a chain of c dependent pivot steps, so warp
-// shuffles (pivot arg-max) and __syncwarp replace block barriers; each lane owns rows
-// (and later columns of L^-1) lane and lane + 32.
+//
+// One CTA of four warps per matrix.  GB300 issues FP64 FMAs at about half a lane per clock
+// per SM sub-partition, so the factorisation is bound by FP64 issue: the work of every step
+// is spread over all four warps (one per sub-partition) with every lane busy.
+//  * Factorisation (left-looking): rows of L are kept by original index (no row swaps); at
+//    pivot step k every remaining row o needs L[o,k] = (M[o,pk] - sum_{j<k} L[o,j] L[pk,j])
+//    / L[pk,pk].  The R remaining rows go to groups of tpr threads (the largest power of two
+//    with tpr * R <= 128), groups dealt round robin over the warps; a group's threads take
+//    every tpr-th j and combine their sums by shuffles.
+//  * L11^{-1} (pivot order), row by row: Li[i,j] = -(sum_{t=j}^{i-1} L[i,t] Li[t,j]) / L[i,i]
+//    for j < i.  Outputs j and i-1-j are paired (i + 1 terms per pair, i - j and j + 1) so
+//    that every group has the same amount of work.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(32)
+constexpr int kPcThreads = 128;
+
+__global__ void __launch_bounds__(kPcThreads)
 pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* dims, int dstride,
              int cmax, double relTol, double* __restrict__ T, int ldt, long long bsT,
              int* rank, int rstride)
 {
     extern __shared__ double sm[];
     constexpr int SS = kMaxC + 1;
-    double* L = sm;                    // L[i*SS + k], i in pivot-position order
-    double* Mi = L + kMaxC * SS;       // copy of M
-    double* Li = Mi + kMaxC * SS;      // L11^{-1}
-    __shared__ double dg[kMaxC];
-    __shared__ double invd[kMaxC];     // 1 / L[k][k] (one reciprocal per pivot)
-    __shared__ int perm[kMaxC];
+    double* Lo = sm;                   // Lo[o*SS + j]: L of original row o, pivot step j
+    double* Li = Lo + kMaxC * SS;      // Li[i*SS + j]: (L11^{-1})[i, j], pivot order
+    __shared__ double dg[kMaxC];       // remaining diagonal, by original index
+    __shared__ double invd[kMaxC];     // 1 / L[k, k] (one reciprocal square root per pivot)
+    __shared__ int piv[kMaxC];         // original index of pivot k
+    __shared__ int rl[kMaxC];          // remaining original indices, positions 0 .. m-1
     const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int b = blockIdx.x;
     int c = cmax;
     if (dims) c = min(dims[b * dstride], cmax);
     if (c < 0) c = 0;
     const double* Mb = M + b * bsM;
-    for (int e = lane; e < c * c; e += 32) {
-        const int i = e % c, j = e / c;
-        Mi[i * SS + j] = Mb[i + (long long)j * ldm];
-    }
-    for (int i = lane; i < kMaxC; i += 32) perm[i] = i;
-    __syncwarp();
+    for (int i = tid; i < c; i += kPcThreads) { dg[i] = Mb[i + (long long)i * ldm]; rl[i] = i; }
+    __syncthreads();
     double mx = 0.0;
-    for (int i = lane; i < c; i += 32) { dg[i] = Mi[i * SS + i]; mx = fmax(mx, dg[i]); }
-    const double dmax0 = warp_max(mx);
-    __syncwarp();
-    int rk = c;
+    for (int i = lane; i < c; i += 32) mx = fmax(mx, dg[i]);
+    const double dmax0 = warp_max(mx);      // every warp alike
+    int m = c, rk = c;
     for (int k = 0; k < c; ++k) {
-        // pivot: largest remaining diagonal among positions k..c-1 (ties: smallest position)
+        // pivot: largest remaining diagonal (ties: smallest original index), every warp alike
         double best = -1.0;
-        int bp = c;
-        for (int p = k + lane; p < c; p += 32) {
-            const double v = dg[perm[p]];
-            if (v > best || (v == best && p < bp)) { best = v; bp = p; }
+        int bo = kMaxC, bp = -1;
+        for (int p = lane; p < m; p += 32) {
+            const int o = rl[p];
+            const double v = dg[o];
+            if (v > best || (v == best && o < bo)) { best = v; bo = o; bp = p; }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(full, best, o);
-            const int op = __shfl_xor_sync(full, bp, o);
-            if (ob > best || (ob == best && op < bp)) { best = ob; bp = op; }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ob = __shfl_xor_sync(full, best, off);
+            const int oo = __shfl_xor_sync(full, bo, off);
+            const int op = __shfl_xor_sync(full, bp, off);
+            if (ob > best || (ob == best && oo < bo)) { best = ob; bo = oo; bp = op; }
         }
         if (!(best > relTol * dmax0) || !(best > 0.0)) { rk = k; break; }   // uniform
-        if (bp != k) {
-            // rows of L are stored by pivot position: move the computed part with the pivot
-            if (lane == 0) { const int t = perm[k]; perm[k] = perm[bp]; perm[bp] = t; }
-            for (int j = lane; j < k; j += 32) {
-                const double x = L[k * SS + j]; L[k * SS + j] = L[bp * SS + j]; L[bp * SS + j] = x;
-            }
-            __syncwarp();
-        }
         const double ik = fc_rsqrt(best);
-        const double lkk = best * ik;
-        if (lane == 0) { L[k * SS + k] = lkk; invd[k] = ik; }
-        const int pk = perm[k];
-        for (int i = k + 1 + lane; i < c; i += 32) {
-            // four independent accumulators: a dependent FP64 FMA costs 64 cycles on GB300
-            double s0 = Mi[perm[i] * SS + pk], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int j = 0;
-            for (; j + 4 <= k; j += 4) {
-                s0 = fma(-L[i * SS + j], L[k * SS + j], s0);
-                s1 = fma(-L[i * SS + j + 1], L[k * SS + j + 1], s1);
-                s2 = fma(-L[i * SS + j + 2], L[k * SS + j + 2], s2);
-                s3 = fma(-L[i * SS + j + 3], L[k * SS + j + 3], s3);
+        const int pk = bo;
+        // the R = m - 1 other remaining rows: group g = slot * 4 + warp, slot = lane / tpr
+        const int R = m - 1;
+        int tpr = 32;
+        while (tpr > 1 && tpr * R > kPcThreads) tpr >>= 1;
+        const int slot = lane / tpr, sub = lane - slot * tpr, g = slot * 4 + wid;
+        double s0 = 0.0, s1 = 0.0;
+        int o = -1;
+        if (g < R) {
+            o = rl[g < bp ? g : g + 1];                 // positions other than the pivot's
+            const double* Lr = Lo + o * SS;
+            const double* Lk = Lo + pk * SS;
+            int j = sub;
+            for (; j + tpr < k; j += 2 * tpr) {
+                s0 = fma(Lr[j], Lk[j], s0);
+                s1 = fma(Lr[j + tpr], Lk[j + tpr], s1);
             }
-            for (; j < k; ++j) s0 = fma(-L[i * SS + j], L[k * SS + j], s0);
-            s0 = (s0 + s1) + (s2 + s3);
-            const double l = s0 * ik;
-            L[i * SS + k] = l;
-            dg[perm[i]] -= l * l;
+            if (j < k) s0 = fma(Lr[j], Lk[j], s0);
         }
-        __syncwarp();
+        double sdot = s0 + s1;
+        for (int off = tpr >> 1; off > 0; off >>= 1) sdot += __shfl_xor_sync(full, sdot, off);
+        if (o >= 0 && sub == 0) {
+            const double l = (Mb[o + (long long)pk * ldm] - sdot) * ik;
+            Lo[o * SS + k] = l;
+            dg[o] -= l * l;
+        }
+        __syncthreads();                   // every read of rl, dg and row pk of this step done
+        if (tid == 0) {
+            Lo[pk * SS + k] = best * ik;
+            invd[k] = ik;
+            piv[k] = pk;
+            rl[bp] = rl[m - 1];
+        }
+        --m;
+        __syncthreads();
     }
     const int r = rk;
-    // L11^{-1} (lower triangular): column j by lane j (and j + 32), forward substitution
-    for (int j = lane; j < r; j += 32) {
-        for (int i = 0; i < j; ++i) Li[i * SS + j] = 0.0;
-        Li[j * SS + j] = invd[j];
-        for (int i = j + 1; i < r; ++i) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int t = j;
-            for (; t + 4 <= i; t += 4) {
-                s0 = fma(-L[i * SS + t], Li[t * SS + j], s0);
-                s1 = fma(-L[i * SS + t + 1], Li[(t + 1) * SS + j], s1);
-                s2 = fma(-L[i * SS + t + 2], Li[(t + 2) * SS + j], s2);
-                s3 = fma(-L[i * SS + t + 3], Li[(t + 3) * SS + j], s3);
+    // ---- L11^{-1}, row by row; pair (a, bb) = (p, i-1-p), the middle output alone ----------
+    for (int i = 0; i < r; ++i) {
+        const double* Lr = Lo + piv[i] * SS;   // row i of L in pivot order
+        const int np = (i + 1) / 2;            // pairs of outputs j < i
+        int tpr = 32;
+        while (tpr > 1 && tpr * np > kPcThreads) tpr >>= 1;
+        const int slot = lane / tpr, sub = lane - slot * tpr, g = slot * 4 + wid;
+        double acc_a = 0.0, acc_b = 0.0;
+        int a = -1, bb = -1;
+        if (g < np) {
+            a = g;
+            bb = i - 1 - g;                    // == a for the middle output of an odd i
+            const int na = i - a, ntot = (bb == a) ? na : i + 1;
+            int u = sub;
+            for (; u < na; u += tpr) acc_a = fma(Lr[a + u], Li[(a + u) * SS + a], acc_a);
+            for (; u < ntot; u += tpr) {
+                const int t = bb + (u - na);
+                acc_b = fma(Lr[t], Li[t * SS + bb], acc_b);
             }
-            for (; t < i; ++t) s0 = fma(-L[i * SS + t], Li[t * SS + j], s0);
-            s0 = (s0 + s1) + (s2 + s3);
-            Li[i * SS + j] = s0 * invd[i];
         }
+        for (int off = tpr >> 1; off > 0; off >>= 1) {
+            acc_a += __shfl_xor_sync(full, acc_a, off);
+            acc_b += __shfl_xor_sync(full, acc_b, off);
+        }
+        if (a >= 0 && sub == 0) {
+            Li[i * SS + a] = -invd[i] * acc_a;
+            if (bb != a) Li[i * SS + bb] = -invd[i] * acc_b;
+        }
+        if (tid == 0) Li[i * SS + i] = invd[i];
+        __syncthreads();
     }
-    __syncwarp();
-    // R11^{-1} = (L11^T)^{-1} = (L11^{-1})^T ; T[perm[j], i] = Rinv[j, i] = Linv[i, j]
+    // R11^{-1} = (L11^T)^{-1} = (L11^{-1})^T ; T[piv[j], i] = Rinv[j, i] = Li[i, j]
     double* Tb = T + b * bsT;
-    for (int e = lane; e < cmax * cmax; e += 32) Tb[(e % cmax) + (long long)(e / cmax) * ldt] = 0.0;
-    __syncwarp();
-    for (int e = lane; e < r * r; e += 32) {
+    for (int e = tid; e < cmax * cmax; e += kPcThreads) Tb[(e % cmax) + (long long)(e / cmax) * ldt] = 0.0;
+    __syncthreads();
+    for (int e = tid; e < r * r; e += kPcThreads) {
         const int j = e % r, i = e / r;
-        if (j <= i) Tb[perm[j] + (long long)i * ldt] = Li[i * SS + j];
+        if (j <= i) Tb[piv[j] + (long long)i * ldt] = Li[i * SS + j];
     }
-    if (lane == 0) rank[b * rstride] = r;
+    if (tid == 0) rank[b * rstride] = r;
 }
 
-size_t pchol_smem() { return sizeof(double) * 3 * kMaxC * (kMaxC + 1); }
+size_t pchol_smem() { return sizeof(double) * 2 * kMaxC * (kMaxC + 1); }
 
 cudaError_t set_linalg_attributes()
 {
@@ -137,8 +164,8 @@ void launch_pchol(cudaStream_t st, int batch, const double* M, int ldm, long lon
 {
     if (batch <= 0) return;
     const size_t sm = pchol_smem();
-    note_launch(); pchol_kernel<<<batch, 32, sm, st>>>(M, ldm, bsM, dims, dstride, cmax, relTol, T, ldt, bsT,
-                                         rank, rstride);
+    note_launch(); pchol_kernel<<<batch, kPcThreads, sm, st>>>(M, ldm, bsM, dims, dstride, cmax,
+                                                               relTol, T, ldt, bsT, rank, rstride);
 }
 
 // ---------------------------------------------------------------------------------------
