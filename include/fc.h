@@ -77,11 +77,14 @@ typedef struct fc_setup_opts {
     int precision;      /* 0: FP64 contractions; 1: the large contractions (DST, Khatri-Rao  */
                         /* projections, Tucker core) in double-float arithmetic on the FP32  */
                         /* pipe (hi + lo FP32 pairs, ~1e-14 relative), 64x GB300's FP64 rate; */
-                        /* 2: contractions of >= 2^24 multiply-adds on the BF16 tensor cores  */
+                        /* 2: contractions of >= 2^tc_min_log2 (fc_schedule) multiply-adds on */
+                        /* the BF16 tensor cores                                              */
                         /* as exact products of 7-bit fixed-point digits of the FP64 operands */
                         /* (8 digits, FP32-exact accumulation, error below FP64 rounding of  */
-                        /* the row/column scales).  Eigen-solves, sketch Grams and scalars   */
-                        /* stay FP64 in every form [0]                                        */
+                        /* the row/column scales), the truncation's Grams and bases and the  */
+                        /* inner products' cross-Grams included.  The small eigen-solves and  */
+                        /* Cholesky factors and the PCG scalars stay FP64 in every form, and  */
+                        /* form 1 keeps the Grams of the truncation FP64 [0]                  */
     int op_kind;        /* operator (Section 6, Tables 6.1-6.4): 0 the control operator      */
                         /* beta^2 A^-alpha + gamma A^alpha (A^alpha + A^-alpha at beta =      */
                         /* gamma = 1); 1 A^alpha; 2 I + A^(2 alpha) (needs 2 alpha <= 1).     */
@@ -242,7 +245,7 @@ typedef struct fc_schedule {
                         /* CTA per SM, 0 = fewest K ranges of <= 448; 0..1 [1]                  */
     int tc_min_log2;    /* contraction form 3 sends contractions of >= 2^tc_min_log2           */
                         /* multiply-adds to the tensor cores, smaller ones to the FP64 GEMM;   */
-                        /* 10..40 [24]                                                          */
+                        /* 10..40 [22]                                                          */
     int workers;        /* fc_solve_batched host threads and worker streams; 1..64 [16]       */
     int order;          /* fc_solve_batched: 0 = problems in the given order, 1 = largest n^d  */
                         /* first (then largest right-hand-side rank); 0..1 [0]                 */
@@ -349,8 +352,8 @@ int fc_symeig(int method, int batch, int m, const double* dev_A, int lda, long l
 /* C = alpha op(A) op(B) + beta C for column-major FP64 device matrices (op(A) M x K, op(B)
  * K x N; op = transpose if transA / transB), in the given contraction form: 0 the FP64 tiled
  * GEMM, 1 double-float on the FP32 pipe, 2 the BF16 tensor cores with 8 fixed-point digits
- * per operand (any size; the solver routes only contractions of >= 2^24 multiply-adds
- * there).  This is the contraction kernel of every form of the solver, exposed for testing
+ * per operand (any size; the solver routes contractions of at least 2^tc_min_log2
+ * multiply-adds there, fc_schedule).  This is the contraction kernel of every form of the solver, exposed for testing
  * and reuse: the paper has no counterpart of it.  All pointers are device pointers owned by
  * the caller; lda >= rows of A as stored, etc.  Asynchronous on `stream`; FC_ETIMEOUT (form
  * 2) only after a synchronisation of the stream inside the call.  Errors: FC_EINVAL. */

@@ -519,7 +519,7 @@ int truncate_impl(fc_ctx* h, cudaStream_t st, const KRIn* kr, const DenseIn* dn,
     if (kr) {
         // budget scale: the norm of the column-normalised weights,
         // sum_{k,j} (xa_k xb_j)^2 prod_l nu_l(k,j)^2 with nu_l(k,j)^2 = ((E_l.E_l)^T (Yh_l.Yh_l))[k,j]
-        gemm(st, kr->Ra, kr->S, n, LdSqT{kr->E, n, kr->bsE}, LdSqN{kr->Yh, n, (long long)n * h->KIN},
+        gemm_p(bp, st, kr->Ra, kr->S, n, LdSqT{kr->E, n, kr->bsE}, LdSqN{kr->Yh, n, (long long)n * h->KIN},
              1.0, 0.0, w.Nu, kr->Ra, (long long)std::max(h->RA, h->RP) * h->KIN, d);
         launch_inner_reduce(st, d, kr->Ra, kr->S, kr->xa, kr->xb, w.Nu, kr->Ra,
                             (long long)std::max(h->RA, h->RP) * h->KIN, w.scal + 4, true);
@@ -692,9 +692,12 @@ int inner_impl(fc_ctx* h, cudaStream_t st, const CP& x, const CP& y, double* out
     if (x.rank == 0 || y.rank == 0) { *out = 0.0; return FC_OK; }
     if (x.rank > h->KIN || y.rank > h->KIN) return FC_ERANK;
     const long long kk = (long long)h->KIN * h->KIN;
+    // the cross-Grams of the factors: tensor-core digits in form 3 (FP64-accurate), else FP64;
+    // the recurrence itself (the weighted sum below and the scalars) is FP64 in every form
+    const int bp = (h->prec == GP_TC64) ? GP_TC64 : GP_F64;
     for (int l = 0; l < h->d; ++l)
-        gemm(st, x.rank, y.rank, h->n, LdT{x.U[l], x.ld, 0}, LdN{y.U[l], y.ld, 0}, 1.0, 0.0,
-             h->w.Mi + l * kk, x.rank);
+        gemm_p(bp, st, x.rank, y.rank, h->n, LdT{x.U[l], x.ld, 0}, LdN{y.U[l], y.ld, 0}, 1.0, 0.0,
+               h->w.Mi + l * kk, x.rank);
     launch_inner_reduce(st, h->d, x.rank, y.rank, x.xi, y.xi, h->w.Mi, x.rank, kk, h->w.scal + 20);
     CKL();
     CK(cudaMemcpyAsync(h->hbuf, h->w.scal + 20, sizeof(double), cudaMemcpyDeviceToHost, st));

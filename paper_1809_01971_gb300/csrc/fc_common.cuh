@@ -32,7 +32,7 @@ struct SchedState {
     std::atomic<int> gemm_cover{8};     // FP64 GEMM tiles: cover gemm_cover / 8 of the SMs
     std::atomic<int> gemm_split{4};     // split-K until about gemm_split CTAs per SM (0: never)
     std::atomic<int> tc_split{1};       // tensor-core K ranges: 1 fill the waves, 0 fewest
-    std::atomic<int> tc_min_log2{24};   // form 3: tensor cores from 2^tc_min_log2 multiply-adds
+    std::atomic<int> tc_min_log2{22};   // form 3: tensor cores from 2^tc_min_log2 multiply-adds
     std::atomic<int> workers{16};       // fc_solve_batched host threads / worker streams
     std::atomic<int> order{0};          // fc_solve_batched: 0 given order, 1 largest first
 };
@@ -355,7 +355,7 @@ namespace fc {
 // tiles and fewer splits waste less).
 // Precision of a contraction: FP64, double-float on the FP32 pipe (gemm_df_kernel), or
 // FP64-accurate digit products on the BF16 tensor cores (gemm_tc_kernel) for contractions
-// of at least 2^tc_min_log2 [2^24] multiply-adds (smaller ones stay on the FP64 kernel,
+// of at least 2^tc_min_log2 [2^22] multiply-adds (smaller ones stay on the FP64 kernel,
 // whose latency is lower).
 enum GemmPrec { GP_F64 = 0, GP_DF32 = 1, GP_TC64 = 2 };
 

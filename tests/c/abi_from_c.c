@@ -29,7 +29,7 @@ int main(void) {
         fc_schedule s0, s1, best;
         int calls = 0, evals = 0;
         double c = 0.0;
-        if (fc_get_schedule(&s0) != FC_OK || s0.workers != 16 || s0.tc_min_log2 != 24) bad |= 128;
+        if (fc_get_schedule(&s0) != FC_OK || s0.workers != 16 || s0.tc_min_log2 != 22) bad |= 128;
         s1 = s0;
         s1.workers = 0;
         if (fc_set_schedule(&s1) != FC_EINVAL) bad |= 256;

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 # the two corners of the autotuner's search space, and the default
 SPLIT_ALL = dict(gemm_cover=1, gemm_split=8, tc_split=1, tc_min_log2=20, workers=8, order=1)
 SPLIT_NONE = dict(gemm_cover=16, gemm_split=0, tc_split=0, tc_min_log2=26, workers=32, order=0)
-DEFAULT = dict(gemm_cover=8, gemm_split=4, tc_split=1, tc_min_log2=24, workers=16, order=0)
+DEFAULT = dict(gemm_cover=8, gemm_split=4, tc_split=1, tc_min_log2=22, workers=16, order=0)
 
 
 @pytest.fixture(scope="module")

@@ -10,7 +10,7 @@ from paper_1809_01971_gb300 import fc
 FIELDS = ("gemm_cover", "gemm_split", "tc_split", "tc_min_log2", "workers", "order")
 CANDIDATES = {"gemm_cover": (1, 2, 4, 8, 16), "gemm_split": (0, 1, 2, 4, 8), "tc_split": (0, 1),
               "tc_min_log2": (20, 22, 24, 26), "workers": (8, 16, 24, 32), "order": (0, 1)}
-DEFAULT = dict(gemm_cover=8, gemm_split=4, tc_split=1, tc_min_log2=24, workers=16, order=0)
+DEFAULT = dict(gemm_cover=8, gemm_split=4, tc_split=1, tc_min_log2=22, workers=16, order=0)
 # evaluations of one full pass from a start on the candidate lists: every other value of
 # every field
 PASS = sum(len(v) - 1 for v in CANDIDATES.values())
