@@ -13,19 +13,76 @@ namespace fc {
 // with rank r and pivot order piv, Y P[:, :r] = Q R11, and T[:, :r] = P[:, :r] R11^{-1}
 // (T zero elsewhere) gives Q = Y T with orthonormal first r columns.  rank[b*rstride] = r.
 //
-// One CTA of four warps per matrix.  GB300 issues FP64 FMAs at about half a lane per clock
-// per SM sub-partition, so the factorisation is bound by FP64 issue: the work of every step
-// is spread over all four warps (one per sub-partition) with every lane busy.
-//  * Factorisation (left-looking): rows of L are kept by original index (no row swaps); at
-//    pivot step k every remaining row o needs L[o,k] = (M[o,pk] - sum_{j<k} L[o,j] L[pk,j])
-//    / L[pk,pk].  The R remaining rows go to groups of tpr threads (the largest power of two
-//    with tpr * R <= 128), groups dealt round robin over the warps; a group's threads take
-//    every tpr-th j and combine their sums by shuffles.
-//  * L11^{-1} (pivot order), row by row: Li[i,j] = -(sum_{t=j}^{i-1} L[i,t] Li[t,j]) / L[i,i]
-//    for j < i.  Outputs j and i-1-j are paired (i + 1 terms per pair, i - j and j + 1) so
-//    that every group has the same amount of work.
+// One CTA of four warps per matrix, one block barrier per pivot step.  GB300 issues FP64 FMAs
+// at about half a lane per clock per SM sub-partition and a dependent FP64 operation takes
+// ~64 cycles, so the work of every step is spread over all four warps with every lane busy,
+// and the steps are kept short:
+//  * the remaining rows are a 64-bit mask held by every thread (no shared list); the g-th
+//    remaining row is the g-th set bit;
+//  * step k: every warp finds the pivot pk (largest remaining diagonal, ties: smallest
+//    index); the R other remaining rows go to groups of tpr threads (the largest power of
+//    two with tpr * R <= 128, dealt round robin over the warps) for
+//    L[o,k] = (M[o,pk] - sum_{j<k} L[o,j] L[pk,j]) / L[pk,pk] (every tpr-th j per thread,
+//    combined by shuffles; M[o,pk] is loaded before the sums);
+//  * in the same step, row k-1 of L11^{-1} (pivot order):
+//    Li[i,j] = -(sum_{t=j}^{i-1} L[i,t] Li[t,j]) / L[i,i], outputs j and i-1-j paired so every
+//    group has i + 1 terms.
+// Rows of L are kept by original index (no row swaps).
 // ---------------------------------------------------------------------------------------
 constexpr int kPcThreads = 128;
+
+// Index of the g-th (from 0) set bit of m (m has more than g bits set).
+FC_DEV int nth_set_bit(unsigned long long m, int g) {
+    unsigned w = (unsigned)m;
+    int base = 0, r = g;
+    const int pl = __popc(w);
+    if (r >= pl) { r -= pl; w = (unsigned)(m >> 32); base = 32; }
+    int p = __popc(w & 0xFFFFu);
+    if (r >= p) { r -= p; w >>= 16; base += 16; }
+    p = __popc(w & 0xFFu);
+    if (r >= p) { r -= p; w >>= 8; base += 8; }
+    p = __popc(w & 0xFu);
+    if (r >= p) { r -= p; w >>= 4; base += 4; }
+    p = __popc(w & 0x3u);
+    if (r >= p) { r -= p; w >>= 2; base += 2; }
+    if (r >= (int)(w & 1u)) base += 1;
+    return base;
+}
+
+// Row i of L11^{-1} (pivot order) from rows 0..i-1 and row i of L; see the kernel's comment.
+FC_DEV void pchol_inverse_row(int i, const double* Lo, double* Li, const int* piv,
+                              const double* invd, int lane, int wid)
+{
+    constexpr int SS = kMaxC + 1;
+    const unsigned full = 0xffffffffu;
+    const double* Lr = Lo + piv[i] * SS;
+    const int np = (i + 1) / 2;            // pairs of outputs j < i
+    int tpr = 32;
+    while (tpr > 1 && tpr * np > kPcThreads) tpr >>= 1;
+    const int slot = lane / tpr, sub = lane - slot * tpr, g = slot * 4 + wid;
+    double acc_a = 0.0, acc_b = 0.0;
+    int a = -1, bb = -1;
+    if (g < np) {
+        a = g;
+        bb = i - 1 - g;                    // == a for the middle output of an odd i
+        const int na = i - a, ntot = (bb == a) ? na : i + 1;
+        int u = sub;
+        for (; u < na; u += tpr) acc_a = fma(Lr[a + u], Li[(a + u) * SS + a], acc_a);
+        for (; u < ntot; u += tpr) {
+            const int t = bb + (u - na);
+            acc_b = fma(Lr[t], Li[t * SS + bb], acc_b);
+        }
+    }
+    for (int off = tpr >> 1; off > 0; off >>= 1) {
+        acc_a += __shfl_xor_sync(full, acc_a, off);
+        acc_b += __shfl_xor_sync(full, acc_b, off);
+    }
+    if (a >= 0 && sub == 0) {
+        Li[i * SS + a] = -invd[i] * acc_a;
+        if (bb != a) Li[i * SS + bb] = -invd[i] * acc_b;
+    }
+    if (lane == 0 && wid == 0) Li[i * SS + i] = invd[i];
+}
 
 __global__ void __launch_bounds__(kPcThreads)
 pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* dims, int dstride,
@@ -36,10 +93,12 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
     constexpr int SS = kMaxC + 1;
     double* Lo = sm;                   // Lo[o*SS + j]: L of original row o, pivot step j
     double* Li = Lo + kMaxC * SS;      // Li[i*SS + j]: (L11^{-1})[i, j], pivot order
-    __shared__ double dg[kMaxC];       // remaining diagonal, by original index
+    // remaining diagonal by original index, double-buffered: step k reads dg[k & 1] (every
+    // warp's pivot search) and its updates go to dg[(k + 1) & 1], so no warp can see a value
+    // of step k's updates while another still searches
+    __shared__ double dg[2][kMaxC];
     __shared__ double invd[kMaxC];     // 1 / L[k, k] (one reciprocal square root per pivot)
     __shared__ int piv[kMaxC];         // original index of pivot k
-    __shared__ int rl[kMaxC];          // remaining original indices, positions 0 .. m-1
     const unsigned full = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int b = blockIdx.x;
@@ -47,40 +106,45 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
     if (dims) c = min(dims[b * dstride], cmax);
     if (c < 0) c = 0;
     const double* Mb = M + b * bsM;
-    for (int i = tid; i < c; i += kPcThreads) { dg[i] = Mb[i + (long long)i * ldm]; rl[i] = i; }
+    for (int i = tid; i < c; i += kPcThreads) dg[0][i] = Mb[i + (long long)i * ldm];
     __syncthreads();
     double mx = 0.0;
-    for (int i = lane; i < c; i += 32) mx = fmax(mx, dg[i]);
+    for (int i = lane; i < c; i += 32) mx = fmax(mx, dg[0][i]);
     const double dmax0 = warp_max(mx);      // every warp alike
-    int m = c, rk = c;
-    for (int k = 0; k < c; ++k) {
+    unsigned long long rem = (c >= 64) ? ~0ull : ((1ull << c) - 1ull);   // remaining rows
+    int rk = c;
+    for (int k = 0; k <= c; ++k) {
+        if (k > 0) pchol_inverse_row(k - 1, Lo, Li, piv, invd, lane, wid);
+        if (k == c) break;
         // pivot: largest remaining diagonal (ties: smallest original index), every warp alike
+        const double* dcur = dg[k & 1];
+        double* dnxt = dg[(k + 1) & 1];
         double best = -1.0;
-        int bo = kMaxC, bp = -1;
-        for (int p = lane; p < m; p += 32) {
-            const int o = rl[p];
-            const double v = dg[o];
-            if (v > best || (v == best && o < bo)) { best = v; bo = o; bp = p; }
-        }
+        int bo = kMaxC;
+        for (int o = lane; o < c; o += 32)
+            if ((rem >> o) & 1ull) {
+                const double v = dcur[o];
+                if (v > best || (v == best && o < bo)) { best = v; bo = o; }
+            }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const double ob = __shfl_xor_sync(full, best, off);
             const int oo = __shfl_xor_sync(full, bo, off);
-            const int op = __shfl_xor_sync(full, bp, off);
-            if (ob > best || (ob == best && oo < bo)) { best = ob; bo = oo; bp = op; }
+            if (ob > best || (ob == best && oo < bo)) { best = ob; bo = oo; }
         }
         if (!(best > relTol * dmax0) || !(best > 0.0)) { rk = k; break; }   // uniform
-        const double ik = fc_rsqrt(best);
         const int pk = bo;
-        // the R = m - 1 other remaining rows: group g = slot * 4 + warp, slot = lane / tpr
-        const int R = m - 1;
+        rem &= ~(1ull << pk);
+        // the R other remaining rows: group g = slot * 4 + warp, slot = lane / tpr
+        const int R = __popcll(rem);
         int tpr = 32;
         while (tpr > 1 && tpr * R > kPcThreads) tpr >>= 1;
         const int slot = lane / tpr, sub = lane - slot * tpr, g = slot * 4 + wid;
-        double s0 = 0.0, s1 = 0.0;
+        double s0 = 0.0, s1 = 0.0, mo = 0.0;
         int o = -1;
         if (g < R) {
-            o = rl[g < bp ? g : g + 1];                 // positions other than the pivot's
+            o = nth_set_bit(rem, g);
+            if (sub == 0) mo = Mb[o + (long long)pk * ldm];
             const double* Lr = Lo + o * SS;
             const double* Lk = Lo + pk * SS;
             int j = sub;
@@ -90,55 +154,23 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
             }
             if (j < k) s0 = fma(Lr[j], Lk[j], s0);
         }
+        const double ik = fc_rsqrt(best);
         double sdot = s0 + s1;
         for (int off = tpr >> 1; off > 0; off >>= 1) sdot += __shfl_xor_sync(full, sdot, off);
         if (o >= 0 && sub == 0) {
-            const double l = (Mb[o + (long long)pk * ldm] - sdot) * ik;
+            const double l = (mo - sdot) * ik;
             Lo[o * SS + k] = l;
-            dg[o] -= l * l;
+            dnxt[o] = dcur[o] - l * l;
         }
-        __syncthreads();                   // every read of rl, dg and row pk of this step done
         if (tid == 0) {
             Lo[pk * SS + k] = best * ik;
             invd[k] = ik;
             piv[k] = pk;
-            rl[bp] = rl[m - 1];
         }
-        --m;
         __syncthreads();
     }
+    __syncthreads();                       // the last inverse row
     const int r = rk;
-    // ---- L11^{-1}, row by row; pair (a, bb) = (p, i-1-p), the middle output alone ----------
-    for (int i = 0; i < r; ++i) {
-        const double* Lr = Lo + piv[i] * SS;   // row i of L in pivot order
-        const int np = (i + 1) / 2;            // pairs of outputs j < i
-        int tpr = 32;
-        while (tpr > 1 && tpr * np > kPcThreads) tpr >>= 1;
-        const int slot = lane / tpr, sub = lane - slot * tpr, g = slot * 4 + wid;
-        double acc_a = 0.0, acc_b = 0.0;
-        int a = -1, bb = -1;
-        if (g < np) {
-            a = g;
-            bb = i - 1 - g;                    // == a for the middle output of an odd i
-            const int na = i - a, ntot = (bb == a) ? na : i + 1;
-            int u = sub;
-            for (; u < na; u += tpr) acc_a = fma(Lr[a + u], Li[(a + u) * SS + a], acc_a);
-            for (; u < ntot; u += tpr) {
-                const int t = bb + (u - na);
-                acc_b = fma(Lr[t], Li[t * SS + bb], acc_b);
-            }
-        }
-        for (int off = tpr >> 1; off > 0; off >>= 1) {
-            acc_a += __shfl_xor_sync(full, acc_a, off);
-            acc_b += __shfl_xor_sync(full, acc_b, off);
-        }
-        if (a >= 0 && sub == 0) {
-            Li[i * SS + a] = -invd[i] * acc_a;
-            if (bb != a) Li[i * SS + bb] = -invd[i] * acc_b;
-        }
-        if (tid == 0) Li[i * SS + i] = invd[i];
-        __syncthreads();
-    }
     // R11^{-1} = (L11^T)^{-1} = (L11^{-1})^T ; T[piv[j], i] = Rinv[j, i] = Li[i, j]
     double* Tb = T + b * bsT;
     for (int e = tid; e < cmax * cmax; e += kPcThreads) Tb[(e % cmax) + (long long)(e / cmax) * ldt] = 0.0;
