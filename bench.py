@@ -363,14 +363,15 @@ def main(argv=None):
         sched, cost, evals = fc.fc_autotune_batched(
             [hs[i] for i in idx], [Bs[i] for i in idx], [Us[i] for i in idx],
             tol=[probs[i].tol for i in idx], eps=[probs[i].eps for i in idx], precision=prec,
-            spectral=spectral, stall=STALL, passes=1, min_gain=0.02, stream=main_stream)
+            spectral=spectral, stall=STALL, passes=1, min_gain=0.05, stream=main_stream)
         tuner = {"schedule": sched.as_dict(), "default": default_schedule, "evaluations": evals,
                  "seconds": time.perf_counter() - t_tune,
                  "first_slice_solves_per_s": {"default (forms survey)": survey[best]["value"],
                                               "tuned": 1.0 / cost if cost > 0 else None},
-                 "search": "coordinate descent over the schedule fields, one pass, 2 % "
-                           "margin; cost = device seconds per converged solve of one batched "
-                           "run of the first slice"}
+                 "search": "coordinate descent over the schedule fields, one pass, 5 % "
+                           "margin (one run of 64 problems per candidate varies by 3-5 %); "
+                           "cost = device seconds per converged solve of one batched run of "
+                           "the first slice"}
     # the headline: warm-up and exactly K timed steps of the chosen form
     counter["step"] = 0
     for _ in range(args.warmup):
@@ -467,6 +468,16 @@ def main(argv=None):
     return 0 if err_best <= args.max_err else 3
 
 
+# DRAM traffic per launch of each kernel class (dram__bytes_read.sum + dram__bytes_write.sum
+# from one ncu capture, caches flushed before every launch, so first-touch traffic), averaged
+# over the launches of one 3D n = 2047 solve of the mixed batch in the tensor-core spectral form
+# (problem 7; profiles/dram_traffic_n2047_tc64_spectral.md).  The sample below has n <= 1023, so
+# its launches move less; the figure bounds what a launch of the class reads and writes.
+TRAFFIC_N2047 = {3: 1.472e6, 2: 7.309e6, 1: 0.423e6}
+TRAFFIC_SOURCE = ("ncu capture of one n = 2047 solve (problem 7, tensor-core spectral form), "
+                  "mean DRAM bytes per launch of the class, caches flushed before each launch")
+
+
 def kernel_rooflines(fc, hs, Bs, Us, probs, sample, form, stream):
     """Achieved rate of the three kernel classes that carry the solve's work (the FP64 tiled
     GEMM, the tensor-core digit GEMM, the graded eigen-solver) over the sample's solves, each
@@ -476,8 +487,9 @@ def kernel_rooflines(fc, hs, Bs, Us, probs, sample, form, stream):
     peaks = measured_peaks()
     alu = alu_peaks()
     specs = [
-        (fc.fc.PROF_F64, "gemm_kernel (FP64 tiled GEMM: Grams, bases, inner products, the "
-                         "contractions below 2^24 multiply-adds)", "alu", alu["fp64_tflops"],
+        (fc.fc.PROF_F64, "gemm_kernel (FP64 tiled GEMM: the contractions below the "
+                         "tensor-core threshold and the Tucker core's small Grams)", "alu",
+         alu["fp64_tflops"],
          "FP64 pipe, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
          "2 flop per multiply-add of the live tiles"),
         (fc.fc.PROF_TC, "gemm_tc_kernel (FP64-accurate contractions as BF16 digit-pair MMAs on "
@@ -502,7 +514,8 @@ def kernel_rooflines(fc, hs, Bs, Us, probs, sample, form, stream):
             continue
         achieved = work / (ms * 1e-3) / 1e12
         out.append({"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": TRAFFIC_N2047.get(kclass), "traffic_source": TRAFFIC_SOURCE,
                     "peak_kind": peak_kind, "work": work_kind, "launches": n_launch,
                     "event_ms": ms, "avg_launch_us": 1e3 * ms / n_launch,
                     "timing": f"isolated launches over {len(sample)} sample solves run one "

@@ -23,7 +23,7 @@ namespace fc {
 //    index); the R other remaining rows go to groups of tpr threads (the largest power of
 //    two with tpr * R <= 128, dealt round robin over the warps) for
 //    L[o,k] = (M[o,pk] - sum_{j<k} L[o,j] L[pk,j]) / L[pk,pk] (every tpr-th j per thread,
-//    combined by shuffles; M[o,pk] is loaded before the sums);
+//    combined by shuffles; M is copied to shared memory once);
 //  * in the same step, row k-1 of L11^{-1} (pivot order):
 //    Li[i,j] = -(sum_{t=j}^{i-1} L[i,t] Li[t,j]) / L[i,i], outputs j and i-1-j paired so every
 //    group has i + 1 terms.
@@ -93,6 +93,8 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
     constexpr int SS = kMaxC + 1;
     double* Lo = sm;                   // Lo[o*SS + j]: L of original row o, pivot step j
     double* Li = Lo + kMaxC * SS;      // Li[i*SS + j]: (L11^{-1})[i, j], pivot order
+    double* Ms = Li + kMaxC * SS;      // Ms[o*SS + p] = M[o, p] (an L2 read per step would sit
+                                       // on the critical path)
     // remaining diagonal by original index, double-buffered: step k reads dg[k & 1] (every
     // warp's pivot search) and its updates go to dg[(k + 1) & 1], so no warp can see a value
     // of step k's updates while another still searches
@@ -106,7 +108,12 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
     if (dims) c = min(dims[b * dstride], cmax);
     if (c < 0) c = 0;
     const double* Mb = M + b * bsM;
-    for (int i = tid; i < c; i += kPcThreads) dg[0][i] = Mb[i + (long long)i * ldm];
+    for (int e = tid; e < c * c; e += kPcThreads) {
+        const int i = e % c, j = e / c;
+        Ms[i * SS + j] = Mb[i + (long long)j * ldm];
+    }
+    __syncthreads();
+    for (int i = tid; i < c; i += kPcThreads) dg[0][i] = Ms[i * SS + i];
     __syncthreads();
     double mx = 0.0;
     for (int i = lane; i < c; i += 32) mx = fmax(mx, dg[0][i]);
@@ -144,7 +151,7 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
         int o = -1;
         if (g < R) {
             o = nth_set_bit(rem, g);
-            if (sub == 0) mo = Mb[o + (long long)pk * ldm];
+            if (sub == 0) mo = Ms[o * SS + pk];
             const double* Lr = Lo + o * SS;
             const double* Lk = Lo + pk * SS;
             int j = sub;
@@ -182,7 +189,7 @@ pchol_kernel(const double* __restrict__ M, int ldm, long long bsM, const int* di
     if (tid == 0) rank[b * rstride] = r;
 }
 
-size_t pchol_smem() { return sizeof(double) * 2 * kMaxC * (kMaxC + 1); }
+size_t pchol_smem() { return sizeof(double) * 3 * kMaxC * (kMaxC + 1); }
 
 cudaError_t set_linalg_attributes()
 {
