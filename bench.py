@@ -471,8 +471,9 @@ def main(argv=None):
 # DRAM traffic per launch of each kernel class (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture, caches flushed before every launch, so first-touch traffic), averaged
 # over the launches of one 3D n = 2047 solve of the mixed batch in the tensor-core spectral form
-# (problem 7; profiles/dram_traffic_n2047_tc64_spectral.md).  The sample below has n <= 1023, so
-# its launches move less; the figure bounds what a launch of the class reads and writes.
+# (problem 7, the command-line solve `--batch 7:8 --precision 2 --spectral` under ncu).  The
+# sample below has n <= 1023, so its launches move less; the figure bounds what a launch of the
+# class reads and writes.
 TRAFFIC_N2047 = {3: 1.472e6, 2: 7.309e6, 1: 0.423e6}
 TRAFFIC_SOURCE = ("ncu capture of one n = 2047 solve (problem 7, tensor-core spectral form), "
                   "mean DRAM bytes per launch of the class, caches flushed before each launch")
